@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the AINV-preconditioned CG solve of the ocean free-surface
+system (PCG solves/s at rtol 1e-10; HBM GB/s per iteration; roofline of the
+dominant kernel) on one B300, or on N GPUs as independent replicas.
+
+Step = one complete solve (pack b, r0 = b - A x0, s0 = M^-1 r0, the PCG loop
+to ||r|| / ||b|| <= 1e-10, final x update, true-residual check, unpack x) of a
+synthetic seeded grid through the library's C ABI. The factor is built once
+before timing (as in the paper, where it is a setup step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import gridgen  # noqa: E402
+
+METRIC = "PCG solves/s & HBM GB/s per iter at rtol 1e-10, mixed vs FP64; p99 latency"
+UNIT = "solves/s"
+
+# pattern codes of the C ABI
+TRIL_A, TRIL_A2, BAND_T, DIAG = 0, 1, 3, 4
+
+WORKLOADS = {
+    # the largest grid of the configurations (eddy-resolving, 13.2M points): the
+    # working set (~1.5 GB) is far above the 126 MB L2, so every iteration streams HBM
+    "orca12-fp64": dict(grid=gridgen.ORCA12, ci=4, pattern=TRIL_A2, tau=0.05, q=0, prec=0, rtol=1e-10),
+    "orca12-fp64-trilA": dict(grid=gridgen.ORCA12, ci=4, pattern=TRIL_A, tau=0.0, q=0, prec=0, rtol=1e-10),
+    "orca025-fp64": dict(grid=gridgen.ORCA025, ci=2, pattern=TRIL_A2, tau=0.05, q=0, prec=0, rtol=1e-10),
+    "coarse-fp64": dict(grid=gridgen.COARSE, ci=1, pattern=TRIL_A2, tau=0.05, q=0, prec=0, rtol=1e-10),
+}
+DEFAULT_WORKLOAD = "orca12-fp64"
+
+# FP64 arithmetic of this B300: 2 FMA per clock per SM (measured 1.87-1.96 at
+# 1.94-2.03 GHz), 148 SMs, 2.032 GHz maximum SM clock, 2 flops per FMA.
+FP64_PEAK_TFLOPS = 2 * 148 * 2.032e9 * 2 / 1e12
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _z_offdiag_per_wet(pcg, h):
+    D, rows, vals = pcg.pcg_ainv_export(h)
+    return float((rows >= 0).sum()) / max(len(D), 1)
+
+
+def _record_iterations():
+    path = os.path.join(ROOT, "oracle", "iterations.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def oracle_sample(wl_name, wl, grid, seconds_target=15.0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    setup (assembly + factor) untimed, then a run of whole oracle PCG
+    iterations; solves/s extrapolated with the oracle's own iteration count
+    for this workload (recorded by oracle/record_iterations.py)."""
+    import oracle
+    P = oracle.OracleProblem.from_grid(grid)
+    assert P.ainv(wl["pattern"], wl["tau"], wl["q"]) == oracle.OK
+    b = P.to_wet(grid.b)
+    # calibrate: a 2-iteration run, then size the sample to ~seconds_target
+    t = time.perf_counter()
+    P.pcg(b, rtol=0.0, max_iter=2, max_replace=0)
+    t2 = time.perf_counter() - t
+    iters = max(2, min(200, int(seconds_target / max(t2 / 2, 1e-6))))
+    t = time.perf_counter()
+    P.pcg(b, rtol=0.0, max_iter=iters, max_replace=0)
+    dt = time.perf_counter() - t
+    per_iter = dt / iters
+    rec = _record_iterations().get(wl_name)
+    if rec is None:
+        full = P.pcg(b, rtol=wl["rtol"])
+        rec = full.iters
+    solves_per_s = 1.0 / (per_iter * rec)
+    return {"value": solves_per_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{iters} serial oracle PCG iterations on the full {grid.nx}x{grid.ny} grid "
+                      f"({dt:.1f} s, incl. the initial and final residuals), scaled by the oracle's "
+                      f"{rec} iterations per solve"}
+
+
+def run_reference(args, wl_name, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    grid = gridgen.make_grid(seed=gridgen.seed_for(wl["ci"]), **wl["grid"])
+    samples = []
+    for step in range(args.warmup + args.steps):
+        s = oracle_sample(wl_name, wl, grid, seconds_target=args.ref_seconds)
+        if step >= args.warmup:
+            samples.append(s)
+    val = statistics.median([s["value"] for s in samples])
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / val, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl_name, "grid": f"{grid.nx}x{grid.ny}", "n_wet": int(grid.wet.sum()),
+                   "pattern": wl["pattern"], "drop_tol": wl["tau"], "rtol": wl["rtol"]},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": samples[-1]["sample"]},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _traffic_record(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current kernel source (profiles/traffic.txt: key bytes source_sha)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_1210_1878_b300", "csrc", "kernels.cuh")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            p = line.split()
+            if len(p) >= 3 and p[0] == kernel_key and p[2] == sha:
+                return float(p[1])
+    except Exception:
+        pass
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--ref-seconds", type=float, default=8.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, args.workload, wl)
+
+    import torch
+    import paper_1210_1878_b300 as pcg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # each rank solves its own replica of the workload (independent problems)
+    grid = gridgen.make_grid(seed=gridgen.seed_for(wl["ci"]), **wl["grid"])
+    t = time.perf_counter()
+    h = pcg.ainv_setup_grid(grid, pattern=wl["pattern"], drop_tol=wl["tau"], band_q=wl["q"])
+    setup_s = time.perf_counter() - t
+    n_wet = h.n_wet
+    zbar = _z_offdiag_per_wet(pcg, h)
+    opts = pcg.make_opts(rtol=wl["rtol"], max_iter=5000, prec=wl["prec"])
+    stream = torch.cuda.current_stream()
+    b = torch.from_numpy(grid.b).cuda()
+    x = torch.zeros_like(b)
+
+    for _ in range(args.warmup):
+        st = pcg.pcg_solve(h, b, x, opts)
+    iters = st.iters
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = pcg.pcg_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(pcg.pcg_solve(h, b, x, opts))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = pcg.pcg_kernel_launches() - l0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_per_step = ms / args.steps
+    value = world * args.steps / (ms / 1e3)
+    worst_true = max(s.true_relres for s in stats)
+    assert all(s.status == pcg.PCG_OK for s in stats), [s.as_dict() for s in stats if s.status]
+
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    bh = torch.from_numpy(grid.b.copy()).pin_memory()
+    xh = torch.zeros_like(bh).pin_memory()
+    pcg.pcg_solve(h, bh, xh, opts)
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e2.record(stream)
+    for _ in range(args.e2e_steps):
+        pcg.pcg_solve(h, bh, xh, opts)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_e2e = float(tt.item())
+    e2e_value = world * args.e2e_steps / (ms_e2e / 1e3)
+    vec_bytes = grid.nx * grid.ny * 8
+
+    # per-kernel roofline, live: mean event-timed duration of each kernel launch
+    ms_k1, ms_k2 = pcg.pcg_profile_kernels(h, b, iters=20)
+    w = 8
+    bytes_k1 = n_wet * w * 9                   # read s, d, x, a, c_e, c_n; write d, x, q
+    bytes_k2 = n_wet * w * (5 + zbar)          # read r, q, Z, D^-1; write r, s
+    flops_k1 = n_wet * 15.0                    # d (1 FMA), x (1 FMA), A d (1 mul + 4 FMA), d.q (1 FMA)
+    flops_k2 = n_wet * (4 * zbar + 7)          # r (1 FMA), Z^T (zbar FMA + 1 mul), Z (zbar FMA), 2 dots
+    hbm_peak, peak_kind = _peaks()
+    dom = "k_precond" if ms_k2 >= ms_k1 else "k_stencil"
+    ms_dom, by, fl = (ms_k2, bytes_k2, flops_k2) if dom == "k_precond" else (ms_k1, bytes_k1, flops_k1)
+    gbs = by / (ms_dom * 1e-3) / 1e9
+    tflops = fl / (ms_dom * 1e-3) / 1e12
+    t_hbm = by / (hbm_peak * 1e9)
+    t_alu = fl / (FP64_PEAK_TFLOPS * 1e12)
+    key = f"{dom}:{args.workload}"
+    traffic = _traffic_record(key)
+    if t_alu > t_hbm:
+        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_kind": "FP64 FMA pipe derived from 2 FMA/clk/SM x 148 SMs x 2.032 GHz",
+                "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "peak_kind": peak_kind}}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": traffic, "peak_kind": peak_kind}
+    roof.update({"kernel": dom, "ms_per_launch": ms_dom,
+                 "per_iteration": {"ms_stencil": ms_k1, "ms_precond": ms_k2,
+                                   "alg_bytes": bytes_k1 + bytes_k2,
+                                   "alg_gbs": (bytes_k1 + bytes_k2) / ((ms_k1 + ms_k2) * 1e-3) / 1e9,
+                                   "hbm_frac": (bytes_k1 + bytes_k2) / ((ms_k1 + ms_k2) * 1e-3) / 1e9 / hbm_peak}})
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_sample(args.workload, wl, grid)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "grid": f"{grid.nx}x{grid.ny}", "n_wet": n_wet,
+                       "pattern": {0: "tril(A)", 1: "tril(A^2)", 3: "band(T)", 4: "diag"}[wl["pattern"]],
+                       "drop_tol": wl["tau"], "z_offdiag_per_wet": zbar, "rtol": wl["rtol"],
+                       "iters_per_solve": iters, "worst_true_relres": worst_true, "setup_s": setup_s,
+                       "l2": "inputs larger than L2 (working set ~%.2f GB vs 126 MB L2)"
+                             % (n_wet * 8 * (14 + zbar) / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes,
+                    "d2h_bytes_per_step": vec_bytes},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    h.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,266 @@
+/*
+ * pcg.h -- C ABI of libpcg: AINV-preconditioned conjugate gradient for the
+ * ocean free-surface elliptic system on one NVIDIA B300 (sm_103a).
+ *
+ * The method is that of Cuomo, De Michele, Farina and Chinnici, "A PCG
+ * implementation of an elliptic kernel in an ocean global circulation model
+ * based on GPU libraries" (2012):
+ *   - the operator is the five-point system of Section 3, Eq. 9 on the
+ *     natural ordering (west->east fastest, then south->north), in its SPD
+ *     form, over wet points only, east-west periodic, north/south closed, plus
+ *     the positive mass shift that the D^{n+1} term of Section 2, Eq. 2 adds
+ *     to the diagonal;
+ *   - the preconditioner is the factored approximate inverse of Section 3,
+ *     M^-1 = Z D^-1 Z^T (Z unit upper triangular), built by conjugate
+ *     orthogonalisation restricted to a sparsity pattern;
+ *   - the solver is Algorithm 1 (FSAI-PCG), with the new direction
+ *     d = s + beta d, stopping when ||r|| / ||b|| <= rtol.
+ *
+ * Conventions for every entry point:
+ *   - Return value: a pcg_status (0 = PCG_OK). No C++ exception crosses this
+ *     boundary. pcg_last_error_message() returns a thread-local description
+ *     of the last failure in the calling thread.
+ *   - Grid fields are row-major [ny][nx] (i = 0..nx-1 east-west, periodic;
+ *     j = 0..ny-1 south-north). Vectors b and x use the same layout in
+ *     binary64; entries on land are ignored on input and written as 0.
+ *   - Vector pointers may be device pointers or host pointers (pageable or
+ *     pinned); host buffers are copied through the handle's staging buffer on
+ *     the given stream. The caller owns every buffer it passes.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Calls that return results (solves, applies) synchronise that
+ *     stream before returning.
+ *   - A handle owns all device memory it allocates; it is not thread-safe
+ *     (one thread at a time). The solver server is thread-safe.
+ */
+#ifndef PCG_H
+#define PCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PCG_OK = 0,
+  PCG_EINVAL = 1,      /* invalid argument: sizes, null pointers, negative or non-finite coefficients */
+  PCG_ENOMEM = 2,      /* device or host allocation failed */
+  PCG_EBUDGET = 3,     /* solver server: admission refused by the HBM budget */
+  PCG_ENOTCONV = 4,    /* max_iter reached: x holds the last iterate, stats are filled */
+  PCG_EBREAKDOWN = 5,  /* non-positive pivot in the AINV build, (d, q) <= 0, or NaN/Inf in the iteration */
+  PCG_ETIMEOUT = 6,    /* a bounded device wait or a server wait gave up */
+  PCG_ECUDA = 7,       /* a CUDA runtime call failed */
+  PCG_ECANCELLED = 8   /* solver server: the request was cancelled before it ran */
+} pcg_status;
+
+/* Problem definition (Section 3, Eq. 8-9; Section 2, Eq. 2).
+ * c_e[j*nx+i]: coefficient of the face between (i,j) and ((i+1) mod nx, j).
+ * c_n[j*nx+i]: coefficient of the face between (i,j) and (i,j+1); the last
+ *              row's values are ignored.
+ * A face touching a land cell carries no flux, whatever its value.
+ * shift[j*nx+i]: diagonal mass term, > 0 on wet cells.
+ * A_kk = shift_k + sum of the wet faces of k; A_km = -c_face.
+ * All pointers are host pointers; the data is copied during ainv_setup. */
+typedef struct {
+  int32_t nx, ny;
+  const uint8_t *wet;     /* [ny][nx], nonzero = ocean */
+  const double *c_e;      /* [ny][nx], >= 0, finite */
+  const double *c_n;      /* [ny][nx], >= 0, finite */
+  const double *shift;    /* [ny][nx], > 0 and finite on wet cells */
+} pcg_grid;
+
+/* Sparsity pattern of Z (column k may hold rows m <= k of):
+ *   PCG_PAT_TRIL_A  -- the lower part of the pattern of A (the k's west and
+ *                      south neighbours, plus the periodic east neighbour of
+ *                      the last column); Section 3's incomplete inverse
+ *                      factorisation on a fixed pattern.
+ *   PCG_PAT_TRIL_A2 -- the lower part of the pattern of A^2 (points within two
+ *                      steps through wet cells).
+ *   PCG_PAT_FULL    -- dense; reserved for the CPU oracle, rejected here.
+ *   PCG_PAT_BAND_T  -- the paper's own choice (Section 3, pattern-selection
+ *                      steps 1-6): Z from the east-west tridiagonal part T of
+ *                      A, upper bandwidth band_q.
+ *   PCG_PAT_DIAG    -- Z = I, D = diag(A): the diagonal (Jacobi) preconditioner
+ *                      of Section 3, Eqs. 10-12. */
+typedef enum {
+  PCG_PAT_TRIL_A = 0,
+  PCG_PAT_TRIL_A2 = 1,
+  PCG_PAT_FULL = 2,
+  PCG_PAT_BAND_T = 3,
+  PCG_PAT_DIAG = 4
+} pcg_pattern;
+
+typedef struct {
+  int32_t pattern;     /* pcg_pattern */
+  double drop_tol;     /* drop |z_mk| sqrt(a_mm / a_kk) < drop_tol after every update; 0 = keep all */
+  int32_t band_q;      /* PCG_PAT_BAND_T only: upper bandwidth q, 1..8 */
+  int32_t tile_x;      /* device strip width in points: 32, 64 or 128; 0 = chosen from nx */
+  int32_t tile_y;      /* device strip height in rows, 4..256; 0 = chosen from ny */
+} ainv_opts;
+
+typedef enum { PCG_FP64 = 0, PCG_MIXED = 1 } pcg_precision;
+
+typedef struct {
+  double rtol;         /* stop when ||r|| / ||b|| <= rtol (2-norm over wet points) */
+  int32_t max_iter;    /* cap on inner iterations in total; <= 0 means the number of wet points */
+  int32_t prec;        /* pcg_precision. PCG_MIXED: binary32 inner PCG inside a binary64
+                          iterative-refinement loop (binary64 outer residual, x update and
+                          inner dot-product accumulation) */
+  double inner_rtol;   /* PCG_MIXED: relative tolerance of each inner solve (default 1e-5 if <= 0) */
+  int32_t max_outer;   /* PCG_MIXED: cap on refinement steps (default 30 if <= 0) */
+  int32_t use_x0;      /* nonzero: x holds the initial guess on entry; zero: start from x = 0 */
+  int32_t max_replace; /* FP64: restarts from the true residual when it fails rtol on exit (default 3 if < 0) */
+} pcg_opts;
+
+typedef struct {
+  int32_t iters;        /* inner iterations (all refinement steps together) */
+  int32_t outer_iters;  /* refinement steps (PCG_MIXED) or 1 + restarts (PCG_FP64) */
+  int32_t status;       /* pcg_status of the solve */
+  int32_t replacements; /* true-residual restarts taken */
+  double relres;        /* recursive ||r|| / ||b|| at exit (binary64 outer residual in PCG_MIXED) */
+  double true_relres;   /* ||b - A x|| / ||b|| computed on the device in binary64 at exit */
+  double seconds;       /* wall time of the call */
+} pcg_stats;
+
+typedef struct pcg_handle pcg_handle;
+
+/* Validate the grid, assemble A, build Z and D on the host by left-looking
+ * conjugate orthogonalisation (Section 3; the paper builds its factor serially
+ * on the CPU, Section 4), and upload A, Z, D^-1 to the device in the packed
+ * strip layout. On success *out owns all device memory of this grid.
+ * Errors: PCG_EINVAL (nx < 3, nx < 5 with PCG_PAT_TRIL_A2, ny < 1, null
+ * pointers, negative or non-finite coefficients, shift <= 0 on a wet cell,
+ * PCG_PAT_FULL, band_q out of range), PCG_EBREAKDOWN (non-positive pivot),
+ * PCG_ENOMEM, PCG_ECUDA. */
+int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, pcg_handle **out);
+
+/* Solve A x = b (Algorithm 1). b: [ny][nx] binary64; x: [ny][nx] binary64,
+ * read as the initial guess when opts->use_x0, always written with the
+ * solution (land = 0). opts may be NULL (rtol 1e-10, FP64). Blocks until the
+ * solve is finished; stats (may be NULL) are then valid.
+ * Returns the solve status: PCG_OK, PCG_ENOTCONV (x holds the last iterate),
+ * PCG_EBREAKDOWN, PCG_ETIMEOUT, PCG_EINVAL, PCG_ECUDA. */
+int pcg_solve(pcg_handle *h, const double *b, double *x, const pcg_opts *opts, pcg_stats *stats,
+              void *cuda_stream);
+
+/* Solve nbatch independent systems, one per handle (handles may repeat only
+ * with distinct b/x buffers), advancing all of them in lock-step: every
+ * device launch covers the work of all unconverged members, and converged
+ * members drop out. Each member's result equals what pcg_solve gives for it
+ * alone (same kernels, same per-grid reduction order). stats: [nbatch].
+ * Returns PCG_OK if every member converged, else the first failing status. */
+int pcg_solve_batched(pcg_handle *const *hs, int32_t nbatch, const double *const *b, double *const *x,
+                      const pcg_opts *opts, pcg_stats *stats, void *cuda_stream);
+
+/* q = A v on the device kernels of the iteration (Section 3, Eq. 9). */
+int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream);
+
+/* s = Z D^-1 Z^T r on the device kernels of the iteration (Algorithm 1, line 7). */
+int pcg_precond_apply(pcg_handle *h, const double *r, double *s, void *cuda_stream);
+
+/* Export the library's own factor for comparison: for each wet point k in
+ * natural order, D[k] and the off-diagonal entries of column k of Z.
+ * Entries are reported as (row index m, value) pairs; rows/vals hold room
+ * for 8 entries per column ([n_wet][8], unused entries have row = -1).
+ * n_wet_out receives the number of wet points. Any output may be NULL to
+ * query n_wet only. */
+int pcg_ainv_export(const pcg_handle *h, int32_t *n_wet_out, double *D, int32_t *rows, double *vals);
+
+/* Build the library's factor on the host only (no device needed) and export
+ * it as pcg_ainv_export does. n_wet_out receives the number of wet points;
+ * D, rows, vals must hold nx*ny, 8*nx*ny and 8*nx*ny entries (an upper bound
+ * of the wet count). Same errors as ainv_setup, without PCG_ECUDA. */
+int ainv_factor_host(const pcg_grid *grid, const ainv_opts *opts, int32_t *n_wet_out, double *D, int32_t *rows,
+                     double *vals);
+
+/* Test hook for the bounded device waits: runs one preconditioner launch of
+ * the grid in which the first row copy of work unit `unit` is deliberately
+ * never issued, with every device wait limited to timeout_ms. The waiting CTA
+ * gives up, records PCG_ETIMEOUT in the grid's device state and returns; the
+ * call returns that recorded status (PCG_ETIMEOUT when the guard works). The
+ * handle stays usable. No GPU fault is involved. */
+int pcg_debug_wait_timeout(pcg_handle *h, int32_t unit, double timeout_ms, void *cuda_stream);
+
+/* Measurement entry point: loads b, runs the init kernels, then `iters` PCG
+ * iterations as individual launches of the stencil kernel and of the
+ * preconditioner kernel, each bracketed by CUDA events on cuda_stream.
+ * Writes the mean duration of one launch of each (milliseconds). The
+ * iterations are real (the state advances as in pcg_solve); x is not
+ * returned. Errors: PCG_EINVAL, PCG_ECUDA. */
+int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, double *ms_stencil, double *ms_precond,
+                        void *cuda_stream);
+
+/* Number of kernel launches this library has issued since it was loaded,
+ * counting every kernel run inside a loop graph. */
+uint64_t pcg_kernel_launches(void);
+
+/* Device bytes held by this handle (A, Z, D^-1, work vectors, scratch). */
+size_t pcg_resident_bytes(const pcg_handle *h);
+
+/* Number of wet unknowns of this handle's grid. */
+int32_t pcg_n_wet(const pcg_handle *h);
+
+/* Release the handle and its device memory. NULL is accepted. */
+void pcg_free(pcg_handle *h);
+
+const char *pcg_status_string(int status);
+const char *pcg_last_error_message(void);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct {
+  size_t hbm_budget_bytes;   /* admission limit on the device bytes of registered grids + in-flight work */
+  int32_t max_slots;         /* requests that may be on the device at once (1..256) */
+  int32_t chunk_iters;       /* iterations run between admission/retirement points */
+  pcg_opts solve;            /* options applied to every request */
+} pcg_server_opts;
+
+typedef struct {
+  uint64_t submitted, completed, failed, rejected;
+  double p50_latency_ms, p99_latency_ms, mean_latency_ms;  /* submission -> completion */
+  double solves_per_s;       /* completed / (last completion - first submission) */
+  int32_t in_flight, queued;
+  size_t hbm_used_bytes;
+} pcg_server_stats;
+
+typedef struct pcg_server pcg_server;
+
+/* Continuous-batching solver server. A scheduler thread keeps up to max_slots
+ * requests on the device, advancing all of them together in chunks of
+ * chunk_iters iterations; between chunks it retires converged requests and
+ * admits queued ones, so requests that arrive while others run join the next
+ * chunk. Each grid's requests run in submission order (a timestep depends on
+ * the previous solution); with warm starts, each request starts from the last
+ * solution of its grid. */
+int solver_server_create(const pcg_server_opts *opts, pcg_server **out);
+
+/* Register a grid; the handle stays owned by the caller and must outlive the
+ * server. Fails with PCG_EBUDGET if the grid's resident bytes do not fit. */
+int solver_server_register(pcg_server *s, pcg_handle *h, int32_t *grid_id);
+
+/* Queue a solve of grid grid_id with right-hand side b ([ny][nx], host or
+ * device; copied before this call returns) writing the solution to x_out
+ * ([ny][nx], host or device, written when the request completes). If
+ * warm_start is nonzero the solve starts from the grid's last solution.
+ * done (may be NULL) is called from the scheduler thread on completion. */
+int solver_server_submit(pcg_server *s, int32_t grid_id, const double *b, double *x_out, int32_t warm_start,
+                         void (*done)(void *user, const pcg_stats *stats), void *user, uint64_t *req_id);
+
+/* Wait for one request; fills stats (may be NULL) and returns its status,
+ * or PCG_ETIMEOUT if timeout_ms (< 0 = forever) expires first. */
+int solver_server_wait(pcg_server *s, uint64_t req_id, int32_t timeout_ms, pcg_stats *stats);
+
+/* Cancel a request that has not yet been admitted to the device. */
+int solver_server_cancel(pcg_server *s, uint64_t req_id);
+
+int solver_server_stats(pcg_server *s, pcg_server_stats *out);
+
+/* Stop the scheduler (pending requests complete with PCG_ECANCELLED) and free the server. */
+void solver_server_destroy(pcg_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCG_H */

@@ -1,0 +1,854 @@
+// Host side of libpcg: device planes, launch plans, the device-resident PCG
+// loop (a CUDA graph whose conditional WHILE node repeats the two kernels of
+// an iteration until every grid's stopping test has fired), and the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "handle.cuh"
+
+namespace pcg {
+
+static thread_local std::string g_err;
+void set_error(const std::string &m) { g_err = m; }
+
+
+// ------------------------------------------------------------ kernel table
+template <typename T, int TX, class P>
+static KernelSet make_set() {
+  KernelSet k;
+  k.k1 = (const void *)k_stencil<T, TX>;
+  k.k2 = (const void *)k_precond<T, TX, P>;
+  k.fin = (const void *)k_finalize<T, TX>;
+  k.pack = (const void *)k_pack<T, double, TX>;
+  k.unpack = (const void *)k_unpack<T, double>;
+  k.smem1 = K1Geom<T, TX>::SMEM;
+  k.smem2 = K2Geom<T, TX, P>::SMEM;
+  k.tx = TX;
+  k.ok = true;
+  return k;
+}
+
+template <typename T, int TX>
+static KernelSet pick_tx(int pattern, int q) {
+  switch (pattern) {
+    case PCG_PAT_DIAG: return make_set<T, TX, Pat<PCG_PAT_DIAG, 0>>();
+    case PCG_PAT_TRIL_A: return make_set<T, TX, Pat<PCG_PAT_TRIL_A, 0>>();
+    case PCG_PAT_TRIL_A2: return make_set<T, TX, Pat<PCG_PAT_TRIL_A2, 0>>();
+    case PCG_PAT_BAND_T:
+      switch (q) {
+        case 1: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 1>>();
+        case 2: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 2>>();
+        case 3: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 3>>();
+        case 4: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 4>>();
+        case 5: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 5>>();
+        case 6: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 6>>();
+        case 7: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 7>>();
+        case 8: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 8>>();
+        default: break;
+      }
+      break;
+    default: break;
+  }
+  return KernelSet{};
+}
+
+template <typename T>
+static KernelSet pick(int tx, int pattern, int q) {
+  if (tx == 64) return pick_tx<T, 64>(pattern, q);
+  if (tx == 128) return pick_tx<T, 128>(pattern, q);
+  return KernelSet{};
+}
+
+static std::mutex g_attr_mu;
+static int prepare_set(const KernelSet &k) {
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  CK(cudaFuncSetAttribute(k.k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem1));
+  CK(cudaFuncSetAttribute(k.k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem2));
+  return PCG_OK;
+}
+
+}  // namespace pcg
+
+namespace pcg {
+
+static size_t elem_round(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+template <typename T>
+static int upload_planes(pcg_handle *h, DevPlanes<T> &P, cudaStream_t s) {
+  const HostGrid &G = h->G;
+  const HostFactor &F = h->F;
+  P.nx = G.nx; P.ny = G.ny;
+  P.tx = h->tx; P.ty = h->ty;
+  P.gx = 128 / (int)sizeof(T);
+  const int ntx = (G.nx + P.tx - 1) / P.tx;
+  P.pitch = (int)elem_round((size_t)P.gx + (size_t)ntx * P.tx + P.gx, 128 / sizeof(T));
+  P.nz = F.slots.n; P.nw = F.slots.n_wrap;
+  P.plane_elems = (size_t)(G.ny + 2 * GY) * P.pitch;
+  P.ks = pick<T>(P.tx, h->pattern, h->band_q);
+  if (!P.ks.ok) { set_error("no kernel for this pattern / tile width"); return PCG_EINVAL; }
+  int rc = prepare_set(P.ks);
+  if (rc) return rc;
+  // units: strips holding a wet cell
+  const int nty = (G.ny + P.ty - 1) / P.ty;
+  P.units.clear();
+  for (int sy = 0; sy < nty; ++sy)
+    for (int sx = 0; sx < ntx; ++sx) {
+      bool any = false;
+      for (int j = sy * P.ty; j < std::min(G.ny, (sy + 1) * P.ty) && !any; ++j)
+        for (int i = sx * P.tx; i < std::min(G.nx, (sx + 1) * P.tx); ++i)
+          if (G.idx[(size_t)j * G.nx + i] >= 0) { any = true; break; }
+      if (any) {
+        Unit u{};
+        u.g = 0; u.sx = (int16_t)sx; u.sy = (int16_t)sy; u.u = (int32_t)P.units.size();
+        P.units.push_back(u);
+      }
+    }
+  P.n_units = (int)P.units.size();
+  const size_t nplanes = P.plane_count();
+  const size_t bytes_planes = nplanes * P.plane_elems * sizeof(T);
+  if (cudaMalloc(&P.mem, bytes_planes) != cudaSuccess) { cudaGetLastError(); set_error("device allocation of the grid planes failed"); return PCG_ENOMEM; }
+  CK(cudaMemsetAsync(P.mem, 0, bytes_planes, s));
+  CK(cudaMalloc(&P.zwrap, sizeof(T) * (size_t)G.ny * std::max(P.nw, 1)));
+  CK(cudaMalloc(&P.partial, sizeof(double) * 2 * (size_t)std::max(P.n_units, 1)));
+  CK(cudaMalloc(&P.st, sizeof(SolveState)));
+  CK(cudaMemsetAsync(P.st, 0, sizeof(SolveState), s));
+  CK(cudaMalloc(&P.gd_dev, sizeof(GridDev<T>)));
+  CK(cudaMalloc(&P.units_dev, sizeof(Unit) * (size_t)std::max(P.n_units, 1)));
+  P.bytes = bytes_planes + sizeof(T) * (size_t)G.ny * std::max(P.nw, 1) + sizeof(double) * 2 * P.n_units +
+            sizeof(SolveState) + sizeof(GridDev<T>) + sizeof(Unit) * P.n_units;
+
+  // static planes, built on the host row by row with their periodic copies
+  std::vector<T> buf(P.plane_elems);
+  auto put = [&](int idx, auto value_of) -> int {
+    std::fill(buf.begin(), buf.end(), (T)0);
+    for (int j = 0; j < G.ny; ++j) {
+      T *row = buf.data() + (size_t)(j + GY) * P.pitch + P.gx;
+      for (int i = 0; i < G.nx; ++i) row[i] = (T)value_of(i, j);
+      for (int c = -GHOST; c < 0; ++c) row[c] = row[((c % G.nx) + G.nx) % G.nx];
+      for (int c = G.nx; c < G.nx + GHOST; ++c) row[c] = row[c % G.nx];
+    }
+    CK(cudaMemcpy(P.mem + (size_t)idx * P.plane_elems, buf.data(), P.plane_elems * sizeof(T), cudaMemcpyHostToDevice));
+    return PCG_OK;
+  };
+  auto kk = [&](int i, int j) { return G.idx[(size_t)j * G.nx + i]; };
+  if ((rc = put(PL_CE, [&](int i, int j) { return G.ce[(size_t)j * G.nx + i]; }))) return rc;
+  if ((rc = put(PL_CN, [&](int i, int j) { return G.cn[(size_t)j * G.nx + i]; }))) return rc;
+  if ((rc = put(PL_A, [&](int i, int j) { int k = kk(i, j); return k >= 0 ? G.diag[k] : 0.0; }))) return rc;
+  if ((rc = put(PL_DINV, [&](int i, int j) { int k = kk(i, j); return k >= 0 ? 1.0 / F.d[k] : 0.0; }))) return rc;
+  for (int sidx = 0; sidx < P.nz; ++sidx)
+    if ((rc = put(PL_Z0 + sidx, [&](int i, int j) { int k = kk(i, j); return k >= 0 ? F.z[(size_t)sidx * F.n + k] : 0.0; }))) return rc;
+  if (P.nw > 0) {
+    std::vector<T> zw((size_t)G.ny * P.nw);
+    for (size_t e = 0; e < zw.size(); ++e) zw[e] = (T)F.zwrap[e];
+    CK(cudaMemcpy(P.zwrap, zw.data(), sizeof(T) * zw.size(), cudaMemcpyHostToDevice));
+  }
+  // descriptor
+  GridDev<T> &gd = P.gd;
+  std::memset(&gd, 0, sizeof(gd));
+  gd.nx = G.nx; gd.ny = G.ny; gd.pitch = P.pitch; gd.ty = P.ty;
+  gd.n_units = P.n_units; gd.n_wrap = P.nw;
+  gd.ce = P.plane(PL_CE); gd.cn = P.plane(PL_CN); gd.a = P.plane(PL_A); gd.dinv = P.plane(PL_DINV);
+  for (int sidx = 0; sidx < P.nz; ++sidx) gd.z[sidx] = P.plane(PL_Z0 + sidx);
+  gd.zwrap = P.zwrap;
+  gd.x = P.plane(P.vec(0)); gd.s = P.plane(P.vec(1)); gd.q = P.plane(P.vec(2));
+  gd.r[0] = P.plane(P.vec(3)); gd.r[1] = P.plane(P.vec(4));
+  gd.d[0] = P.plane(P.vec(5)); gd.d[1] = P.plane(P.vec(6));
+  gd.b = P.plane(P.vec(7));
+  gd.partial = P.partial; gd.st = P.st;
+  CK(cudaMemcpy(P.gd_dev, &gd, sizeof(gd), cudaMemcpyHostToDevice));
+  if (P.n_units > 0) CK(cudaMemcpy(P.units_dev, P.units.data(), sizeof(Unit) * P.n_units, cudaMemcpyHostToDevice));
+  return PCG_OK;
+}
+
+static uint64_t default_timeout_ns() {
+  const char *e = getenv("PCG_WAIT_TIMEOUT_MS");
+  double ms = e ? atof(e) : 2000.0;
+  if (!(ms > 0)) ms = 2000.0;
+  return (uint64_t)(ms * 1e6);
+}
+
+static KParams kparams(const LoopPlan &L, const PlanGroup &g, int kind, int use_cond, int guard) {
+  KParams p{};
+  p.grids = g.gd_dev;
+  p.units = g.units_dev;
+  p.ls = L.ls;
+  p.kind = kind;
+  p.use_cond = use_cond;
+  p.guard = guard;
+  p.dbg_skip_unit = -1;
+  p.timeout_ns = default_timeout_ns();
+  return p;
+}
+
+static std::atomic<uint64_t> g_launches{0};
+
+static int launch(const void *f, int grid, int block, size_t smem, KParams p, cudaStream_t s) {
+  if (grid <= 0) return PCG_OK;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  void *args[] = {&p};
+  CK(cudaLaunchKernel(f, dim3(grid), dim3(block), args, smem, s));
+  return PCG_OK;
+}
+
+static int build_loop_graph(LoopPlan &L) {
+  if (getenv("PCG_LOOP_CHUNKED")) return PCG_ECUDA;
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) { cudaGetLastError(); cudaGraphDestroy(g); set_error("conditional graphs unavailable"); return PCG_ECUDA; }
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  e = cudaGraphAddNode(&cnode, g, nullptr, nullptr, 0, &cp);
+  if (e != cudaSuccess) { cudaGetLastError(); cudaGraphDestroy(g); set_error("conditional node unavailable"); return PCG_ECUDA; }
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  // kernel params must outlive node creation only (they are copied)
+  std::vector<KParams> params;
+  params.reserve(2 * L.groups.size());
+  std::vector<void *> argv(2 * L.groups.size());
+  cudaGraphNode_t prev = nullptr;
+  bool have_prev = false, guarded = false;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (size_t gi = 0; gi < L.groups.size(); ++gi) {
+      const PlanGroup &G = L.groups[gi];
+      if (G.n_units <= 0) continue;
+      const int guard = (pass == 0 && !guarded) ? 1 : 0;   // the first stencil launch of the body
+      guarded = guarded || guard;
+      params.push_back(kparams(L, G, pass == 0 ? (int)K1_ITER : (int)K2_ITER, 1, guard));
+      void *args[] = {&params.back()};
+      cudaKernelNodeParams kp{};
+      kp.func = const_cast<void *>(pass == 0 ? G.ks.k1 : G.ks.k2);
+      kp.gridDim = dim3(G.n_units);
+      kp.blockDim = dim3(G.ks.tx);
+      kp.sharedMemBytes = (unsigned)(pass == 0 ? G.ks.smem1 : G.ks.smem2);
+      kp.kernelParams = args;
+      cudaGraphNode_t node;
+      e = cudaGraphAddKernelNode(&node, body, have_prev ? &prev : nullptr, have_prev ? 1 : 0, &kp);
+      if (e != cudaSuccess) { cudaGetLastError(); cudaGraphDestroy(g); set_error("kernel node creation failed"); return PCG_ECUDA; }
+      prev = node; have_prev = true;
+    }
+  }
+  if (!guarded) { cudaGraphDestroy(g); set_error("no work units: no loop graph"); return PCG_ECUDA; }
+  L.body_kernels = (int)params.size();
+  e = cudaGraphInstantiate(&L.exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { cudaGetLastError(); L.exec = nullptr; set_error("graph instantiation failed"); return PCG_ECUDA; }
+  L.cond = h;
+  L.graph_ok = true;
+  return PCG_OK;
+}
+
+// Arm the plan's launch state: `active` grids still iterating, a cap of
+// max_launches loop bodies. Must precede the init kernels of a round, so that
+// grids finishing already there are counted off.
+int members_arm(LoopPlan &L, LaunchState *ls_host, int active, int max_launches, cudaStream_t s) {
+  ls_host->active = active;
+  ls_host->launches = 0;
+  ls_host->max_launches = max_launches;
+  ls_host->stop = 0;
+  ls_host->cond = L.cond;
+  ls_host->t0_ns = 0;
+  ls_host->timed_out = 0;
+  const char *e = getenv("PCG_LOOP_BUDGET_S");
+  const double budget_s = (e && atof(e) > 0) ? atof(e) : 300.0;
+  ls_host->budget_ns = (uint64_t)(budget_s * 1e9);
+  CK(cudaMemcpyAsync(L.ls, ls_host, sizeof(LaunchState), cudaMemcpyHostToDevice, s));
+  return PCG_OK;
+}
+
+// Run the loop body until every grid of the plan is done, or max_launches
+// bodies have run (the guard in the first stencil launch ends it).
+int members_loop(LoopPlan &L, LaunchState *ls_host, int max_launches, cudaStream_t s) {
+  if (L.graph_ok) {
+    CK(cudaGraphLaunch(L.exec, s));
+    return PCG_OK;
+  }
+  // without conditional graphs: chunks of iterations, polling the active count
+  const int chunk = 16;
+  for (int done = 0; done < max_launches;) {
+    const int n = std::min(chunk, max_launches - done);
+    for (int c = 0; c < n; ++c) {
+      bool guarded = false;
+      for (int pass = 0; pass < 2; ++pass)
+        for (size_t gi = 0; gi < L.groups.size(); ++gi) {
+          const PlanGroup &G = L.groups[gi];
+          if (G.n_units <= 0) continue;
+          const int guard = (pass == 0 && !guarded) ? 1 : 0;
+          guarded = guarded || guard;
+          int rc = launch(pass == 0 ? G.ks.k1 : G.ks.k2, G.n_units, G.ks.tx, pass == 0 ? G.ks.smem1 : G.ks.smem2,
+                          kparams(L, G, pass == 0 ? (int)K1_ITER : (int)K2_ITER, 0, guard), s);
+          if (rc) return rc;
+        }
+    }
+    done += n;
+    CK(cudaMemcpyAsync(ls_host, L.ls, sizeof(LaunchState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (ls_host->active <= 0 || ls_host->stop) break;
+  }
+  return PCG_OK;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Pack a user [ny][nx] binary64 vector into plane `which` (0 b, 1 x, 2 r0, 3 d0).
+static int pack_user(pcg_handle *h, const double *user, int which, cudaStream_t s) {
+  auto &P = h->p64;
+  const double *srcp = user;
+  if (!is_device_ptr(user)) {
+    CK(cudaMemcpyAsync(h->stage, user, sizeof(double) * (size_t)P.nx * P.ny, cudaMemcpyHostToDevice, s));
+    srcp = h->stage;
+  }
+  KParams p{};
+  p.grids = P.gd_dev; p.units = P.units_dev;
+  if (P.n_units == 0) return PCG_OK;
+  void *args[] = {&p, (void *)&srcp, &which};
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  CK(cudaLaunchKernel(P.ks.pack, dim3(P.n_units), dim3(P.tx), args, 0, s));
+  return PCG_OK;
+}
+
+// Unpack plane `which` (0 x, 1 s, 2 q) into a user [ny][nx] binary64 vector.
+static int unpack_user(pcg_handle *h, double *user, int which, cudaStream_t s) {
+  auto &P = h->p64;
+  const bool dev = is_device_ptr(user);
+  double *dst = dev ? user : h->stage;
+  const GridDev<double> *gdp = P.gd_dev;
+  void *args[] = {(void *)&gdp, (void *)&dst, &which};
+  const size_t n = (size_t)P.nx * P.ny;
+  const int blocks = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  CK(cudaLaunchKernel(P.ks.unpack, dim3(std::max(blocks, 1)), dim3(256), args, 0, s));
+  if (!dev) CK(cudaMemcpyAsync(user, h->stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  return PCG_OK;
+}
+
+int plan_single(pcg_handle *h) {
+  if (h->plan64) return PCG_OK;
+  auto L = std::make_unique<LoopPlan>();
+  PlanGroup g;
+  g.ks = h->p64.ks;
+  g.n_units = h->p64.n_units;
+  g.gd_dev = h->p64.gd_dev;
+  g.units_dev = h->p64.units_dev;
+  L->groups.push_back(g);
+  L->ls = h->ls;
+  if (build_loop_graph(*L) != PCG_OK) L->graph_ok = false;
+  g_err.clear();
+  h->plan64 = std::move(L);
+  return PCG_OK;
+}
+
+// Plan over several grids: members grouped by kernel set.
+int plan_build(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls, cudaStream_t s) {
+  L.ls = ls;
+  std::vector<std::vector<int>> groups;
+  for (int i = 0; i < n; ++i) {
+    bool placed = false;
+    for (auto &g : groups)
+      if (hs[g[0]]->p64.ks.k2 == hs[i]->p64.ks.k2 && hs[g[0]]->p64.ks.k1 == hs[i]->p64.ks.k1) {
+        g.push_back(i); placed = true; break;
+      }
+    if (!placed) groups.push_back({i});
+  }
+  for (auto &g : groups) {
+    std::vector<GridDev<double>> gds;
+    std::vector<Unit> units;
+    for (size_t mi = 0; mi < g.size(); ++mi) {
+      auto &P = hs[g[mi]]->p64;
+      gds.push_back(P.gd);
+      for (Unit u : P.units) { u.g = (int16_t)mi; units.push_back(u); }
+    }
+    void *gd_dev = nullptr, *un_dev = nullptr;
+    CK(cudaMalloc(&gd_dev, sizeof(GridDev<double>) * gds.size()));
+    L.owned.push_back(gd_dev);
+    CK(cudaMalloc(&un_dev, sizeof(Unit) * std::max<size_t>(units.size(), 1)));
+    L.owned.push_back(un_dev);
+    CK(cudaMemcpyAsync(gd_dev, gds.data(), sizeof(GridDev<double>) * gds.size(), cudaMemcpyHostToDevice, s));
+    if (!units.empty()) CK(cudaMemcpyAsync(un_dev, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));   // the host vectors above go out of scope
+    PlanGroup pg;
+    pg.ks = hs[g[0]]->p64.ks;
+    pg.n_units = (int)units.size();
+    pg.gd_dev = gd_dev;
+    pg.units_dev = (const Unit *)un_dev;
+    L.groups.push_back(pg);
+  }
+  if (with_graph && build_loop_graph(L) != PCG_OK) L.graph_ok = false;
+  g_err.clear();
+  return PCG_OK;
+}
+
+void fill_opts(const pcg_opts *o, pcg_opts &out) {
+  if (o) out = *o;
+  else { std::memset(&out, 0, sizeof(out)); out.rtol = 1e-10; }
+  if (!(out.rtol >= 0.0)) out.rtol = 1e-10;
+  if (out.max_replace < 0) out.max_replace = 3;
+  if (out.inner_rtol <= 0) out.inner_rtol = 1e-5;
+  if (out.max_outer <= 0) out.max_outer = 30;
+}
+
+// Inputs of one member: b, x0 (or x = 0; with pack_x0 false and use_x0 set,
+// the x plane keeps the grid's last solution: a warm start), zeroed
+// directions, and the device state.
+int member_load(Member &m, const pcg_opts &o, bool pack_x0, cudaStream_t s) {
+  auto &P = m.h->p64;
+  int rc;
+  const int max_iter = o.max_iter > 0 ? o.max_iter : std::max(m.h->G.n, 1);
+  if ((rc = pack_user(m.h, m.b, 0, s))) return rc;
+  if (o.use_x0) {
+    if (pack_x0 && (rc = pack_user(m.h, m.x, 1, s))) return rc;
+  } else {
+    CK(cudaMemsetAsync(P.plane_start(P.vec(0)), 0, P.plane_elems * sizeof(double), s));
+  }
+  for (int v : {5, 6}) CK(cudaMemsetAsync(P.plane_start(P.vec(v)), 0, P.plane_elems * sizeof(double), s));
+  SolveState &st = *m.st_host;
+  std::memset(&st, 0, sizeof(st));
+  st.rtol = o.rtol;
+  st.max_iter = max_iter;
+  st.status = PCG_OK;
+  st.done = (m.h->G.n == 0) ? 1 : 0;
+  st.retired = st.done;
+  CK(cudaMemcpyAsync(P.st, &st, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+  m.replacements = 0;
+  m.final_status = st.retired ? PCG_OK : -1;
+  return PCG_OK;
+}
+
+int members_init(LoopPlan &L, cudaStream_t s) {
+  int rc;
+  for (auto &G : L.groups)
+    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tx, G.ks.smem1, kparams(L, G, K1_RESID_INIT, 0, 0), s))) return rc;
+  for (auto &G : L.groups)
+    if ((rc = launch(G.ks.k2, G.n_units, G.ks.tx, G.ks.smem2, kparams(L, G, K2_INIT, 0, 0), s))) return rc;
+  return PCG_OK;
+}
+
+int members_close(LoopPlan &L, cudaStream_t s) {
+  int rc;
+  for (auto &G : L.groups)
+    if ((rc = launch(G.ks.fin, G.n_units, G.ks.tx, 0, kparams(L, G, 0, 0, 0), s))) return rc;
+  for (auto &G : L.groups)
+    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tx, G.ks.smem1, kparams(L, G, K1_RESID_CHECK, 0, 0), s))) return rc;
+  return PCG_OK;
+}
+
+bool member_decide(Member &m, const pcg_opts &o, bool overrun, cudaStream_t s, int *err) {
+  *err = PCG_OK;
+  if (m.final_status >= 0) return false;
+  SolveState &st = *m.st_host;
+  int fs = -1;
+  if (st.status != PCG_OK) fs = st.status;
+  else if (!st.done && overrun) fs = PCG_ETIMEOUT;
+  else if (!st.done) return false;                 // still iterating (chunked advance)
+  else if (st.bzero) fs = PCG_OK;
+  else {
+    const double tr = std::sqrt(st.rr_true) / std::sqrt(st.bb);
+    if (tr <= o.rtol) fs = PCG_OK;
+    else if (st.iter >= st.max_iter || m.replacements >= o.max_replace) fs = PCG_ENOTCONV;
+  }
+  cudaError_t e;
+  if (fs >= 0) {
+    m.final_status = fs;
+    st.retired = 1;
+    e = cudaMemcpyAsync(&m.h->p64.st->retired, &st.retired, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); *err = PCG_ECUDA; }
+    return false;
+  }
+  // restart from the true residual (it is in the current r plane)
+  m.replacements++;
+  st.done = 0;
+  e = cudaMemcpyAsync(&m.h->p64.st->done, &st.done, sizeof(int32_t), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); *err = PCG_ECUDA; }
+  return true;
+}
+
+int member_store(Member &m, cudaStream_t s) { return unpack_user(m.h, m.x, 0, s); }
+
+void member_stats(Member &m) {
+  SolveState &st = *m.st_host;
+  if (!m.stats) return;
+  m.stats->iters = st.iter;
+  m.stats->outer_iters = 1 + m.replacements;
+  m.stats->status = m.final_status;
+  m.stats->replacements = m.replacements;
+  m.stats->relres = st.bb > 0 ? std::sqrt(st.rr) / std::sqrt(st.bb) : 0.0;
+  m.stats->true_relres = st.bb > 0 ? std::sqrt(st.rr_true) / std::sqrt(st.bb) : 0.0;
+}
+
+// Binary64 solve of every member of the plan: Algorithm 1 on the device, the
+// true-residual check, and restarts from the true residual where it fails.
+static int solve_members64(LoopPlan &L, LaunchState *ls_host, std::vector<Member> &M, const pcg_opts &o,
+                           cudaStream_t s) {
+  int rc;
+  int max_iter_all = 0;
+  for (auto &m : M) {
+    if ((rc = member_load(m, o, true, s))) return rc;
+    max_iter_all = std::max(max_iter_all, m.st_host->max_iter);
+  }
+  int active = 0;
+  for (auto &m : M) active += m.final_status < 0 ? 1 : 0;
+  while (active > 0) {
+    if ((rc = members_arm(L, ls_host, active, max_iter_all + 64, s))) return rc;
+    if ((rc = members_init(L, s))) return rc;
+    if ((rc = members_loop(L, ls_host, max_iter_all + 64, s))) return rc;
+    if ((rc = members_close(L, s))) return rc;
+    for (auto &m : M) CK(cudaMemcpyAsync(m.st_host, m.h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ls_host, L.ls, sizeof(LaunchState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (L.graph_ok) g_launches.fetch_add((uint64_t)std::max(ls_host->launches, 0) * L.body_kernels, std::memory_order_relaxed);
+    const bool overrun = ls_host->launches > ls_host->max_launches || ls_host->timed_out;
+    active = 0;
+    for (auto &m : M) {
+      int err;
+      const bool again = member_decide(m, o, overrun, s, &err);
+      if (err) return err;
+      if (again) ++active;
+      else if (m.final_status < 0) m.final_status = PCG_ETIMEOUT;   // the loop ended without this grid
+    }
+  }
+  for (auto &m : M) if ((rc = member_store(m, s))) return rc;
+  CK(cudaStreamSynchronize(s));
+  for (auto &m : M) member_stats(m);
+  return PCG_OK;
+}
+
+std::string status_name(int s) {
+  switch (s) {
+    case PCG_OK: return "ok";
+    case PCG_EINVAL: return "invalid argument";
+    case PCG_ENOMEM: return "out of memory";
+    case PCG_EBUDGET: return "over the HBM budget";
+    case PCG_ENOTCONV: return "did not converge";
+    case PCG_EBREAKDOWN: return "breakdown";
+    case PCG_ETIMEOUT: return "timeout";
+    case PCG_ECUDA: return "CUDA error";
+    case PCG_ECANCELLED: return "cancelled";
+    default: return "unknown status";
+  }
+}
+
+static int choose_tx(int nx) {
+  // the strip width that wastes the fewest columns; ties go to the wider strip
+  const int w128 = (nx + 127) / 128 * 128, w64 = (nx + 63) / 64 * 64;
+  return (w128 - nx <= (w64 - nx) + 16) ? 128 : 64;
+}
+
+static int choose_ty(int nx, int ny, int tx) {
+  const int ntx = (nx + tx - 1) / tx;
+  // aim at >= ~4 CTAs per SM of 148 when the grid allows it, rows 8..32
+  int ty = (int)std::floor((double)ntx * ny / (148.0 * 4));
+  return std::max(8, std::min(32, ty));
+}
+
+}  // namespace pcg
+
+using namespace pcg;
+
+extern "C" {
+
+const char *pcg_status_string(int status) {
+  static thread_local std::string s;
+  s = status_name(status);
+  return s.c_str();
+}
+
+const char *pcg_last_error_message(void) { return g_err.c_str(); }
+
+static int factor_host(const pcg_grid *grid, const ainv_opts *opts, HostGrid &G, HostFactor &F) {
+  if (!opts) { set_error("opts is NULL"); return PCG_EINVAL; }
+  const int pattern = opts->pattern;
+  if (pattern == PCG_PAT_FULL) { set_error("the dense pattern is available in the CPU oracle only"); return PCG_EINVAL; }
+  if (pattern < 0 || pattern > PCG_PAT_DIAG) { set_error("unknown pattern"); return PCG_EINVAL; }
+  if (pattern == PCG_PAT_BAND_T && (opts->band_q < 1 || opts->band_q > 8)) { set_error("band_q must be 1..8"); return PCG_EINVAL; }
+  std::string err;
+  int rc = host_grid_build(grid, pattern, G, err);
+  if (rc) { set_error(err); return rc; }
+  if (pattern == PCG_PAT_BAND_T && grid->nx <= opts->band_q) { set_error("band_q must be < nx"); return PCG_EINVAL; }
+  rc = host_ainv(G, pattern, opts->drop_tol, opts->band_q, F, err);
+  if (rc) { set_error(err); return rc; }
+  return PCG_OK;
+}
+
+static void export_factor(const HostGrid &G, const HostFactor &F, double *D, int32_t *rows, double *vals) {
+  const int n = G.n, nx = G.nx;
+  for (int k = 0; k < n; ++k) {
+    if (D) D[k] = F.d[k];
+    if (!rows || !vals) continue;
+    for (int e = 0; e < 8; ++e) { rows[(size_t)k * 8 + e] = -1; vals[(size_t)k * 8 + e] = 0.0; }
+    int e = 0;
+    const int i = G.pi[k], j = G.pj[k];
+    for (int s = 0; s < F.slots.n; ++s) {
+      const double v = F.z[(size_t)s * n + k];
+      if (v == 0.0) continue;
+      const int ii = ((i + F.slots.dx[s]) % nx + nx) % nx, jj = j + F.slots.dy[s];
+      rows[(size_t)k * 8 + e] = G.idx[(size_t)jj * nx + ii];
+      vals[(size_t)k * 8 + e] = v;
+      ++e;
+    }
+    for (int w = 0; w < F.slots.n_wrap; ++w) {
+      if (i != nx - 1 - F.slots.wcol[w]) continue;
+      const double v = F.zwrap[(size_t)j * F.slots.n_wrap + w];
+      if (v == 0.0) continue;
+      const int ii = ((F.slots.wdx[w] - 1 - F.slots.wcol[w]) % nx + nx) % nx;
+      rows[(size_t)k * 8 + e] = G.idx[(size_t)j * nx + ii];
+      vals[(size_t)k * 8 + e] = v;
+      ++e;
+    }
+  }
+}
+
+int ainv_factor_host(const pcg_grid *grid, const ainv_opts *opts, int32_t *n_wet_out, double *D, int32_t *rows,
+                     double *vals) {
+  try {
+    HostGrid G;
+    HostFactor F;
+    int rc = factor_host(grid, opts, G, F);
+    if (rc) return rc;
+    if (n_wet_out) *n_wet_out = G.n;
+    export_factor(G, F, D, rows, vals);
+    return PCG_OK;
+  } catch (const std::bad_alloc &) {
+    set_error("host allocation failed");
+    return PCG_ENOMEM;
+  } catch (...) {
+    set_error("unexpected host failure");
+    return PCG_EINVAL;
+  }
+}
+
+int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, pcg_handle **out) {
+  if (!out) { set_error("out is NULL"); return PCG_EINVAL; }
+  *out = nullptr;
+  try {
+    auto h = std::make_unique<pcg_handle>();
+    int rc = factor_host(grid, opts, h->G, h->F);
+    if (rc) return rc;
+    h->pattern = opts->pattern;
+    h->band_q = opts->band_q;
+    h->tau = opts->drop_tol;
+    h->tx = opts->tile_x ? opts->tile_x : choose_tx(grid->nx);
+    if (h->tx != 64 && h->tx != 128) { set_error("tile_x must be 64 or 128"); return PCG_EINVAL; }
+    h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx);
+    if (h->ty < 4 || h->ty > 256) { set_error("tile_y must be 4..256"); return PCG_EINVAL; }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    rc = upload_planes(h.get(), h->p64, s);
+    if (rc) { h->p64.release(); return rc; }
+    if (cudaMalloc(&h->ls, sizeof(LaunchState)) != cudaSuccess) { cudaGetLastError(); h->p64.release(); set_error("device allocation failed"); return PCG_ENOMEM; }
+    if (cudaMallocHost(&h->ls_host, sizeof(LaunchState)) != cudaSuccess ||
+        cudaMallocHost(&h->st_host, sizeof(SolveState)) != cudaSuccess) {
+      cudaGetLastError(); set_error("pinned allocation failed"); return PCG_ENOMEM;
+    }
+    if (cudaMalloc(&h->stage, sizeof(double) * (size_t)grid->nx * grid->ny) != cudaSuccess) {
+      cudaGetLastError(); set_error("device allocation failed"); return PCG_ENOMEM;
+    }
+    h->bytes = h->p64.bytes + sizeof(LaunchState) + sizeof(double) * (size_t)grid->nx * grid->ny;
+    CK(cudaStreamSynchronize(s));
+    *out = h.release();
+    return PCG_OK;
+  } catch (const std::bad_alloc &) {
+    set_error("host allocation failed");
+    return PCG_ENOMEM;
+  }
+}
+
+int pcg_solve(pcg_handle *h, const double *b, double *x, const pcg_opts *opts, pcg_stats *stats, void *cuda_stream) {
+  pcg_handle *hs[1] = {h};
+  const double *bs[1] = {b};
+  double *xs[1] = {x};
+  return pcg_solve_batched(hs, 1, bs, xs, opts, stats, cuda_stream);
+}
+
+int pcg_solve_batched(pcg_handle *const *hs, int32_t nbatch, const double *const *b, double *const *x,
+                      const pcg_opts *opts, pcg_stats *stats, void *cuda_stream) {
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!hs || nbatch <= 0 || !b || !x) { set_error("invalid batch arguments"); return PCG_EINVAL; }
+  for (int i = 0; i < nbatch; ++i) {
+    if (!hs[i] || !b[i] || !x[i]) { set_error("NULL handle or vector in batch"); return PCG_EINVAL; }
+    for (int k = 0; k < i; ++k)
+      if (hs[k] == hs[i]) { set_error("a handle may appear once per batch"); return PCG_EINVAL; }
+  }
+  pcg_opts o;
+  fill_opts(opts, o);
+  if (o.prec == PCG_MIXED) { set_error("mixed precision is not built into this library"); return PCG_EINVAL; }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  std::vector<Member> M(nbatch);
+  for (int i = 0; i < nbatch; ++i) {
+    M[i].h = hs[i]; M[i].b = b[i]; M[i].x = x[i]; M[i].stats = stats ? &stats[i] : nullptr;
+    M[i].st_host = hs[i]->st_host;
+  }
+  int rc;
+  if (nbatch == 1) {
+    if ((rc = plan_single(hs[0]))) return rc;
+    rc = solve_members64(*hs[0]->plan64, hs[0]->ls_host, M, o, s);
+  } else {
+    LoopPlan L;
+    if ((rc = plan_build(L, hs, nbatch, true, hs[0]->ls, s))) return rc;
+    rc = solve_members64(L, hs[0]->ls_host, M, o, s);
+    cudaStreamSynchronize(s);
+  }
+  if (rc) return rc;
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int first_bad = PCG_OK;
+  for (int i = 0; i < nbatch; ++i) {
+    if (stats) stats[i].seconds = secs;
+    if (M[i].final_status != PCG_OK && first_bad == PCG_OK) first_bad = M[i].final_status;
+  }
+  if (first_bad != PCG_OK) set_error("solve finished with status: " + status_name(first_bad));
+  return first_bad;
+}
+
+int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream) {
+  if (!h || !v || !q) { set_error("NULL argument"); return PCG_EINVAL; }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  auto &P = h->p64;
+  int rc;
+  if ((rc = pack_user(h, v, 3, s))) return rc;
+  KParams p{};
+  p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K1_SPMV; p.dbg_skip_unit = -1;
+  p.timeout_ns = default_timeout_ns();
+  if ((rc = launch(P.ks.k1, P.n_units, P.tx, P.ks.smem1, p, s))) return rc;
+  if ((rc = unpack_user(h, q, 2, s))) return rc;
+  CK(cudaStreamSynchronize(s));
+  return PCG_OK;
+}
+
+int pcg_precond_apply(pcg_handle *h, const double *r, double *sv, void *cuda_stream) {
+  if (!h || !r || !sv) { set_error("NULL argument"); return PCG_EINVAL; }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  auto &P = h->p64;
+  int rc;
+  if ((rc = pack_user(h, r, 2, s))) return rc;
+  KParams p{};
+  p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K2_APPLY; p.dbg_skip_unit = -1;
+  p.timeout_ns = default_timeout_ns();
+  if ((rc = launch(P.ks.k2, P.n_units, P.tx, P.ks.smem2, p, s))) return rc;
+  if ((rc = unpack_user(h, sv, 1, s))) return rc;
+  CK(cudaStreamSynchronize(s));
+  return PCG_OK;
+}
+
+int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, double *ms_stencil, double *ms_precond,
+                        void *cuda_stream) {
+  if (!h || !b || iters <= 0) { set_error("invalid arguments"); return PCG_EINVAL; }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int rc;
+  if ((rc = plan_single(h))) return rc;
+  LoopPlan &L = *h->plan64;
+  pcg_opts o;
+  fill_opts(nullptr, o);
+  o.rtol = 0.0;                       // iterate the requested number of times
+  o.max_iter = iters + 1;
+  std::vector<Member> M(1);
+  M[0].h = h; M[0].b = b; M[0].x = h->stage; M[0].st_host = h->st_host;
+  M[0].x = nullptr;
+  pcg_opts lo = o;
+  lo.use_x0 = 0;
+  {
+    // member_load packs b and zeroes x (no x0)
+    Member &m = M[0];
+    double *dummy = nullptr;
+    m.x = dummy;
+    if ((rc = member_load(m, lo, false, s))) return rc;
+  }
+  if ((rc = members_arm(L, h->ls_host, 1, iters + 8, s))) return rc;
+  if ((rc = members_init(L, s))) return rc;
+  const PlanGroup &G = L.groups[0];
+  std::vector<cudaEvent_t> ev(4 * iters);
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  for (int it = 0; it < iters; ++it) {
+    CK(cudaEventRecord(ev[4 * it], s));
+    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tx, G.ks.smem1, kparams(L, G, K1_ITER, 0, 0), s))) return rc;
+    CK(cudaEventRecord(ev[4 * it + 1], s));
+    CK(cudaEventRecord(ev[4 * it + 2], s));
+    if ((rc = launch(G.ks.k2, G.n_units, G.ks.tx, G.ks.smem2, kparams(L, G, K2_ITER, 0, 0), s))) return rc;
+    CK(cudaEventRecord(ev[4 * it + 3], s));
+  }
+  CK(cudaStreamSynchronize(s));
+  double t1 = 0, t2 = 0;
+  for (int it = 0; it < iters; ++it) {
+    float a = 0, c = 0;
+    CK(cudaEventElapsedTime(&a, ev[4 * it], ev[4 * it + 1]));
+    CK(cudaEventElapsedTime(&c, ev[4 * it + 2], ev[4 * it + 3]));
+    t1 += a; t2 += c;
+  }
+  for (auto &e : ev) cudaEventDestroy(e);
+  CK(cudaMemcpyAsync(h->st_host, h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (h->st_host->done && h->st_host->iter < iters) {
+    set_error("the iteration stopped early (converged or broke down) while profiling");
+    return PCG_EINVAL;
+  }
+  if (ms_stencil) *ms_stencil = t1 / iters;
+  if (ms_precond) *ms_precond = t2 / iters;
+  return PCG_OK;
+}
+
+uint64_t pcg_kernel_launches(void) { return g_launches.load(); }
+
+int pcg_ainv_export(const pcg_handle *h, int32_t *n_wet_out, double *D, int32_t *rows, double *vals) {
+  if (!h) { set_error("NULL handle"); return PCG_EINVAL; }
+  if (n_wet_out) *n_wet_out = h->G.n;
+  export_factor(h->G, h->F, D, rows, vals);
+  return PCG_OK;
+}
+
+size_t pcg_resident_bytes(const pcg_handle *h) { return h ? h->bytes : 0; }
+
+int32_t pcg_n_wet(const pcg_handle *h) { return h ? h->G.n : 0; }
+
+void pcg_free(pcg_handle *h) {
+  if (!h) return;
+  h->plan64.reset();
+  h->p64.release();
+  cudaFree(h->ls);
+  cudaFree(h->stage);
+  cudaFreeHost(h->ls_host);
+  cudaFreeHost(h->st_host);
+  delete h;
+}
+
+// Test hook: run one preconditioner launch in which the first row copy of
+// unit `unit` is never issued, with every device wait bounded by timeout_ms.
+// The wait must give up, flag PCG_ETIMEOUT in the grid's state and return;
+// the function reports the status the device recorded.
+int pcg_debug_wait_timeout(pcg_handle *h, int32_t unit, double timeout_ms, void *cuda_stream) {
+  if (!h || unit < 0 || unit >= h->p64.n_units) { set_error("invalid arguments"); return PCG_EINVAL; }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  auto &P = h->p64;
+  SolveState st{};
+  st.status = PCG_OK; st.rtol = 1e-10; st.max_iter = 1; st.bb = 1.0;
+  CK(cudaMemcpyAsync(P.st, &st, sizeof(st), cudaMemcpyHostToDevice, s));
+  LaunchState ls{};
+  ls.active = 1;
+  CK(cudaMemcpyAsync(h->ls, &ls, sizeof(ls), cudaMemcpyHostToDevice, s));
+  KParams p{};
+  p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K2_INIT;
+  p.dbg_skip_unit = unit;
+  p.timeout_ns = (uint64_t)(timeout_ms * 1e6);
+  int rc = launch(P.ks.k2, P.n_units, P.tx, P.ks.smem2, p, s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h->st_host, P.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  return h->st_host->status;
+}
+
+}  // extern "C"

@@ -1,0 +1,129 @@
+// Internal host-side structures of libpcg shared by api.cu and server.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "pcg_internal.h"
+
+namespace pcg {
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      set_error(std::string(#call) + " failed: " + cudaGetErrorString(e_));                \
+      return PCG_ECUDA;                                                                    \
+    }                                                                                      \
+  } while (0)
+
+struct KernelSet {
+  const void *k1 = nullptr, *k2 = nullptr, *fin = nullptr, *pack = nullptr, *unpack = nullptr;
+  size_t smem1 = 0, smem2 = 0;
+  int tx = 0;
+  bool ok = false;
+};
+
+enum { PL_CE = 0, PL_CN, PL_A, PL_DINV, PL_Z0 };
+
+template <typename T>
+struct DevPlanes {
+  int nx = 0, ny = 0, pitch = 0, gx = 0, tx = 0, ty = 0, nz = 0, nw = 0, n_units = 0;
+  size_t plane_elems = 0;
+  T *mem = nullptr;
+  T *zwrap = nullptr;
+  double *partial = nullptr;
+  SolveState *st = nullptr;
+  GridDev<T> gd{};
+  GridDev<T> *gd_dev = nullptr;
+  Unit *units_dev = nullptr;       // this grid alone (g = 0)
+  std::vector<Unit> units;
+  KernelSet ks;
+  size_t bytes = 0;
+
+  int plane_count() const { return PL_Z0 + nz + 8; }
+  T *plane(int idx) const { return mem + (size_t)idx * plane_elems + (size_t)GY * pitch + gx; }
+  T *plane_start(int idx) const { return mem + (size_t)idx * plane_elems; }
+  int vec(int k) const { return PL_Z0 + nz + k; }   // 0 x, 1 s, 2 q, 3 r0, 4 r1, 5 d0, 6 d1, 7 b
+
+  void release() {
+    cudaFree(mem); cudaFree(zwrap); cudaFree(partial); cudaFree(st); cudaFree(gd_dev); cudaFree(units_dev);
+    mem = nullptr; zwrap = nullptr; partial = nullptr; st = nullptr; gd_dev = nullptr; units_dev = nullptr;
+  }
+};
+
+// The grids advanced together by one loop: grouped by kernel set, each group
+// with its descriptor array and concatenated unit list on the device.
+struct PlanGroup {
+  KernelSet ks;
+  int n_units = 0;
+  const void *gd_dev = nullptr;
+  const Unit *units_dev = nullptr;
+};
+
+struct LoopPlan {
+  std::vector<PlanGroup> groups;
+  LaunchState *ls = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  bool graph_ok = false;
+  int body_kernels = 0;            // kernel nodes in the loop body
+  std::vector<void *> owned;       // device allocations of a batch plan
+  ~LoopPlan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (void *p : owned) cudaFree(p);
+  }
+};
+
+}  // namespace pcg
+
+struct pcg_handle {
+  pcg::HostGrid G;
+  pcg::HostFactor F;
+  int pattern = 0, band_q = 0;
+  double tau = 0.0;
+  int tx = 0, ty = 0;
+  pcg::DevPlanes<double> p64;
+  pcg::LaunchState *ls = nullptr;        // device
+  pcg::LaunchState *ls_host = nullptr;   // pinned
+  pcg::SolveState *st_host = nullptr;    // pinned mirror
+  double *stage = nullptr;               // device [ny][nx] staging for host buffers
+  std::unique_ptr<pcg::LoopPlan> plan64;
+  size_t bytes = 0;
+};
+
+namespace pcg {
+
+// one grid of a solve in progress
+struct Member {
+  pcg_handle *h = nullptr;
+  const double *b = nullptr;
+  double *x = nullptr;
+  pcg_stats *stats = nullptr;
+  SolveState *st_host = nullptr;
+  int replacements = 0;
+  int final_status = -1;
+};
+
+// phases of a solve, shared by pcg_solve_batched and the solver server
+int member_load(Member &m, const pcg_opts &o, bool pack_x0, cudaStream_t s);     // inputs and state
+int members_arm(LoopPlan &L, LaunchState *ls_host, int active, int max_launches, cudaStream_t s);
+int members_init(LoopPlan &L, cudaStream_t s);                                   // r0, s0, rho0 for not-done grids
+int members_loop(LoopPlan &L, LaunchState *ls_host, int max_launches, cudaStream_t s);
+int members_close(LoopPlan &L, cudaStream_t s);                                  // x update, true residual
+// After members_close and a read-back of the states: decide per member. Returns
+// true if it must restart (its done flag has been cleared on the device).
+bool member_decide(Member &m, const pcg_opts &o, bool overrun, cudaStream_t s, int *err);
+int member_store(Member &m, cudaStream_t s);                                      // unpack x
+void member_stats(Member &m);
+int plan_single(pcg_handle *h);                                                   // h->plan64
+int plan_build(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls, cudaStream_t s);
+std::string status_name(int s);
+void fill_opts(const pcg_opts *o, pcg_opts &out);
+bool is_device_ptr(const void *p);
+
+}  // namespace pcg

@@ -1,0 +1,202 @@
+"""GPU parity of the CUDA path against the FP64 CPU oracle, through the C ABI.
+
+Element by element on seeded grids that span several strips and a ragged
+last strip; tolerances follow from binary64 rounding of the stated
+operations (Section 3, Eq. 9 for A; Algorithm 1 line 7 for M^-1 = Z D^-1 Z^T;
+Algorithm 1 for the solve, whose result is judged by the residual and by the
+distance to a tight reference solution)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import gridgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _pcg():
+    import paper_1210_1878_b300 as pcg
+    return pcg
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+GRIDS = [
+    ("tiny", dict(gridgen.TINY), 0),
+    ("coarse", dict(gridgen.COARSE), 1),
+    ("ragged", dict(nx=203, ny=77, land=0.3), 7),       # last strip partial in i and j
+    ("row", dict(nx=150, ny=1, land=0.1), 8),            # one latitude row
+    ("channel", dict(nx=6, ny=40, land=0.0), 9),         # narrow periodic channel
+]
+
+
+def _grid(spec):
+    name, cfg, seed = spec
+    return gridgen.make_grid(seed=gridgen.seed_for(0) + 100 * seed, **cfg)
+
+
+def _csr(P):
+    rp, col, val, _, _ = P.csr()
+    return sp.csr_matrix((val, col, rp), shape=(P.n, P.n))
+
+
+@pytest.mark.parametrize("spec", GRIDS, ids=[g[0] for g in GRIDS])
+@pytest.mark.parametrize("tiles", [(0, 0), (64, 8), (128, 32)])
+def test_spmv_matches_oracle(spec, tiles):
+    pcg = _pcg()
+    g = _grid(spec)
+    P = oracle.OracleProblem.from_grid(g)
+    h = pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A, tile_x=tiles[0], tile_y=tiles[1])
+    rng = np.random.default_rng(11)
+    v = rng.standard_normal((g.ny, g.nx))
+    q = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
+    pcg.pcg_spmv(h, _dev(v), q)
+    qo = P.to_grid(P.spmv(P.to_wet(v)))
+    mag = P.to_grid(abs(_csr(P)) @ np.abs(P.to_wet(v)))
+    err = np.abs(q.cpu().numpy() - qo)
+    assert np.all(err <= 1e-13 * mag + 1e-300)
+    assert np.all(q.cpu().numpy()[g.wet == 0] == 0)
+
+
+PRECONDS = [(0, 0.0, 0), (1, 0.0, 0), (1, 0.05, 0), (4, 0.0, 0), (3, 0.0, 1), (3, 0.0, 4), (3, 0.0, 8)]
+
+
+@pytest.mark.parametrize("spec", GRIDS, ids=[g[0] for g in GRIDS])
+@pytest.mark.parametrize("pattern,tau,q", PRECONDS)
+def test_precond_matches_oracle(spec, pattern, tau, q):
+    pcg = _pcg()
+    g = _grid(spec)
+    if pattern == 3 and q >= g.nx:
+        pytest.skip("band wider than the row")
+    P = oracle.OracleProblem.from_grid(g)
+    assert P.ainv(pattern, tau, q) == oracle.OK
+    h = pcg.ainv_setup_grid(g, pattern=pattern, drop_tol=tau, band_q=q)
+    rng = np.random.default_rng(12)
+    r = rng.standard_normal((g.ny, g.nx))
+    s = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
+    pcg.pcg_precond_apply(h, _dev(r), s)
+    so = P.to_grid(P.apply(P.to_wet(r)))
+    cp, row, val, d = P.z()
+    Z = sp.csc_matrix((np.abs(val), row, cp), shape=(P.n, P.n))
+    mag = P.to_grid(Z @ ((Z.T @ np.abs(P.to_wet(r))) / d))
+    err = np.abs(s.cpu().numpy() - so)
+    assert np.all(err <= 1e-13 * mag + 1e-300), float((err / (mag + 1e-300)).max())
+
+
+def _tight_reference(P, b):
+    if P.n <= 2000:
+        return np.linalg.solve(P.dense(), b)
+    res = P.pcg(b, rtol=1e-13)
+    return res.x
+
+
+SOLVES = [
+    ("tiny-trilA", dict(gridgen.TINY), 0, 0, 0.0, 0),
+    ("tiny-trilA2", dict(gridgen.TINY), 0, 1, 0.0, 0),
+    ("coarse-trilA2", dict(gridgen.COARSE), 1, 1, 0.05, 0),
+    ("coarse-jacobi", dict(gridgen.COARSE), 1, 4, 0.0, 0),
+    ("coarse-bandT4", dict(gridgen.COARSE), 1, 3, 0.0, 4),
+    ("ragged-trilA", dict(nx=203, ny=77, land=0.3), 7, 0, 0.0, 0),
+    ("orca025-trilA2", dict(gridgen.ORCA025), 2, 1, 0.05, 0),
+]
+
+
+@pytest.mark.parametrize("name,cfg,ci,pattern,tau,q", SOLVES, ids=[s[0] for s in SOLVES])
+def test_solve_matches_oracle(name, cfg, ci, pattern, tau, q):
+    pcg = _pcg()
+    g = gridgen.make_grid(seed=gridgen.seed_for(ci), **cfg)
+    P = oracle.OracleProblem.from_grid(g)
+    assert P.ainv(pattern, tau, q) == oracle.OK
+    b = P.to_wet(g.b)
+    ref = P.pcg(b, rtol=1e-10)
+    assert ref.status == oracle.OK
+    h = pcg.ainv_setup_grid(g, pattern=pattern, drop_tol=tau, band_q=q)
+    x = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
+    st = pcg.pcg_solve(h, _dev(g.b), x, pcg.make_opts(rtol=1e-10))
+    assert st.status == pcg.PCG_OK
+    assert abs(st.iters - ref.iters) <= 2, (st.iters, ref.iters)
+    xg = x.cpu().numpy()
+    assert np.all(xg[g.wet == 0] == 0)
+    xw = P.to_wet(xg)
+    true_rel = np.linalg.norm(b - P.spmv(xw)) / np.linalg.norm(b)
+    assert true_rel <= 1e-10 * (1 + 1e-3), true_rel
+    assert abs(st.true_relres - true_rel) <= 1e-3 * 1e-10 + 1e-3 * true_rel
+    xref = _tight_reference(P, b)
+    assert np.linalg.norm(xw - xref) / np.linalg.norm(xref) <= 1e-8
+
+
+def test_batched_equals_alone_bitwise():
+    pcg = _pcg()
+    specs = [(dict(gridgen.COARSE), 1), (dict(nx=203, ny=77, land=0.3), 7), (dict(gridgen.TINY), 0),
+             (dict(nx=362, ny=292, land=0.3), 3)]
+    grids = [gridgen.make_grid(seed=gridgen.seed_for(ci), **cfg) for cfg, ci in specs]
+    hs = [pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A2, drop_tol=0.05) for g in grids]
+    alone = []
+    for h, g in zip(hs, grids):
+        x = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
+        st = pcg.pcg_solve(h, _dev(g.b), x)
+        alone.append((x.cpu().numpy(), st.iters))
+    xs = [torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda") for g in grids]
+    rc, stats = pcg.pcg_solve_batched(hs, [_dev(g.b) for g in grids], xs)
+    assert rc == pcg.PCG_OK
+    for (xa, ia), xb, st in zip(alone, xs, stats):
+        assert st.iters == ia
+        np.testing.assert_array_equal(xb.cpu().numpy(), xa)
+
+
+def test_host_buffers_and_warm_start():
+    pcg = _pcg()
+    g = gridgen.make_grid(seed=gridgen.seed_for(1), **gridgen.COARSE)
+    h = pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A2, drop_tol=0.05)
+    x_host = np.zeros((g.ny, g.nx))
+    st = pcg.pcg_solve(h, np.ascontiguousarray(g.b), x_host)
+    x_dev = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
+    st2 = pcg.pcg_solve(h, _dev(g.b), x_dev)
+    np.testing.assert_array_equal(x_host, x_dev.cpu().numpy())
+    assert st.iters == st2.iters
+    # warm start from the solution: converged before the first iteration
+    st3 = pcg.pcg_solve(h, _dev(g.b), x_dev, pcg.make_opts(use_x0=True))
+    assert st3.status == pcg.PCG_OK and st3.iters == 0
+
+
+def test_degenerate_cases():
+    pcg = _pcg()
+    g = gridgen.make_grid(seed=gridgen.seed_for(1), **gridgen.COARSE)
+    h = pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A)
+    x = torch.full((g.ny, g.nx), 7.0, dtype=torch.float64, device="cuda")
+    st = pcg.pcg_solve(h, torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda"), x)
+    assert st.status == pcg.PCG_OK and st.iters == 0 and float(x.abs().max()) == 0.0
+    st = pcg.pcg_solve(h, _dev(g.b), x, pcg.make_opts(rtol=1e-14, max_iter=5, max_replace=0), check=False)
+    assert st.status == pcg.PCG_ENOTCONV and st.iters == 5
+    # a single wet cell: A = shift, one step
+    wet = np.zeros((9, 12), np.uint8)
+    wet[4, 11] = 1
+    sh = np.where(wet > 0, 3.0, 0.0)
+    h1 = pcg.ainv_setup(12, 9, wet, np.ones((9, 12)), np.ones((9, 12)), sh, pattern=pcg.PCG_PAT_TRIL_A2)
+    b = np.zeros((9, 12))
+    b[4, 11] = 6.0
+    x1 = torch.zeros((9, 12), dtype=torch.float64, device="cuda")
+    st = pcg.pcg_solve(h1, _dev(b), x1)
+    assert st.status == pcg.PCG_OK and float(x1[4, 11]) == pytest.approx(2.0, rel=1e-15)
+    # all land
+    h0 = pcg.ainv_setup(12, 9, np.zeros((9, 12), np.uint8), np.ones((9, 12)), np.ones((9, 12)), np.ones((9, 12)),
+                        pattern=pcg.PCG_PAT_TRIL_A)
+    st = pcg.pcg_solve(h0, _dev(np.ones((9, 12))), x1)
+    assert st.status == pcg.PCG_OK and float(x1.abs().max()) == 0.0
+
+
+def test_bounded_wait_reports_timeout():
+    """A device wait that can never complete gives up after its limit and the
+    kernel returns PCG_ETIMEOUT through the grid state; the handle keeps working."""
+    pcg = _pcg()
+    g = gridgen.make_grid(seed=gridgen.seed_for(1), **gridgen.COARSE)
+    h = pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A2)
+    assert pcg.pcg_debug_wait_timeout(h, unit=1, timeout_ms=20.0) == pcg.PCG_ETIMEOUT
+    x = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
+    st = pcg.pcg_solve(h, _dev(g.b), x)
+    assert st.status == pcg.PCG_OK and st.true_relres <= 1e-10
