@@ -156,6 +156,24 @@ int pcg_solve_batched(pcg_handle *const *hs, int32_t nbatch, const double *const
 /* q = A v on the device kernels of the iteration (Section 3, Eq. 9). */
 int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream);
 
+/* q = A v like pcg_spmv, but without allocating anything. The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory where they call it -- an ocean model whose own memory
+ * manager owns the whole device, or code running while an allocation would
+ * break its contract (inside a stream capture, or under a fixed memory budget).
+ * Its scratch (the packed v and q planes and the grid descriptor) lives in a
+ * file-scope device array of 2^21 binary64 values per plane (about 32 MiB in
+ * all), which every GPU that loads the library keeps until the process exits.
+ * v and q must be device pointers ([ny][nx] binary64). Grids whose padded
+ * plane ((ny + 4) rows times the strip-padded row pitch) exceeds 2^21 values are
+ * rejected with PCG_EINVAL and a message giving the limit. The first call on a
+ * device looks up the array's device address with that device current, so make
+ * that first call before any stream capture. All calls share the one array and
+ * each call overwrites it (clearing it first): calls that overlap on the GPU --
+ * from different streams or threads -- race and must not be issued. The call
+ * synchronises cuda_stream before returning. Errors: PCG_EINVAL, PCG_ECUDA. */
+int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void *cuda_stream);
+
 /* s = Z D^-1 Z^T r on the device kernels of the iteration (Algorithm 1, line 7). */
 int pcg_precond_apply(pcg_handle *h, const double *r, double *s, void *cuda_stream);
 

@@ -25,7 +25,7 @@ PCG_PAT_TRIL_A, PCG_PAT_TRIL_A2, PCG_PAT_FULL, PCG_PAT_BAND_T, PCG_PAT_DIAG = ra
 PCG_FP64, PCG_MIXED = 0, 1
 
 EXPORTED = [
-    "ainv_setup", "ainv_factor_host", "pcg_solve", "pcg_solve_batched", "pcg_spmv", "pcg_precond_apply",
+    "ainv_setup", "ainv_factor_host", "pcg_solve", "pcg_solve_batched", "pcg_spmv", "pcg_spmv_noalloc", "pcg_precond_apply",
     "pcg_ainv_export", "pcg_resident_bytes", "pcg_n_wet", "pcg_free", "pcg_status_string",
     "pcg_last_error_message", "pcg_debug_wait_timeout", "pcg_profile_kernels", "pcg_kernel_launches", "solver_server_create", "solver_server_register", "solver_server_submit",
     "solver_server_wait", "solver_server_cancel", "solver_server_stats", "solver_server_destroy",
@@ -87,6 +87,7 @@ def _load():
         "pcg_solve_batched": (C.c_int, [C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(pcg_opts),
                                         C.POINTER(pcg_stats), vp]),
         "pcg_spmv": (C.c_int, [vp, vp, vp, vp]),
+        "pcg_spmv_noalloc": (C.c_int, [vp, vp, vp, vp]),
         "pcg_precond_apply": (C.c_int, [vp, vp, vp, vp]),
         "pcg_ainv_export": (C.c_int, [vp, C.POINTER(i32), vp, vp, vp]),
         "pcg_resident_bytes": (C.c_size_t, [vp]),
@@ -253,6 +254,11 @@ def pcg_spmv(h: Handle, v, q, stream=None):
     rc = lib.pcg_spmv(h.ptr, _ptr(v), _ptr(q), _stream(stream))
     if rc != PCG_OK:
         raise PCGError(rc, "pcg_spmv")
+
+
+def pcg_spmv_noalloc(h: Handle, v, q, stream=None) -> int:
+    """q = A v through the allocation-free entry point; returns the status."""
+    return int(lib.pcg_spmv_noalloc(h.ptr, _ptr(v), _ptr(q), _stream(stream)))
 
 
 def pcg_precond_apply(h: Handle, r, s, stream=None):

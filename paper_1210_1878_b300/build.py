@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["api.cu", "server.cu"]
+CU_SOURCES = ["api.cu", "server.cu", "noalloc.cu"]
 CPP_SOURCES = ["ainv_host.cpp"]
 HEADERS = ["pcg_internal.h", "device.cuh", "kernels.cuh", "handle.cuh"]
 
