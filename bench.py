@@ -43,6 +43,10 @@ WORKLOADS = {
     "orca12-fp64-trilA": dict(grid=gridgen.ORCA12, ci=4, pattern=TRIL_A, tau=0.0, q=0, prec=0, rtol=1e-10),
     "orca025-fp64": dict(grid=gridgen.ORCA025, ci=2, pattern=TRIL_A2, tau=0.05, q=0, prec=0, rtol=1e-10),
     "coarse-fp64": dict(grid=gridgen.COARSE, ci=1, pattern=TRIL_A2, tau=0.05, q=0, prec=0, rtol=1e-10),
+    # binary32 inner PCG inside binary64 iterative refinement, same acceptance (true residual <= 1e-10)
+    "orca12-mixed": dict(grid=gridgen.ORCA12, ci=4, pattern=TRIL_A2, tau=0.05, q=0, prec=1, rtol=1e-10),
+    "orca12-mixed-trilA": dict(grid=gridgen.ORCA12, ci=4, pattern=TRIL_A, tau=0.0, q=0, prec=1, rtol=1e-10),
+    "orca025-mixed": dict(grid=gridgen.ORCA025, ci=2, pattern=TRIL_A2, tau=0.05, q=0, prec=1, rtol=1e-10),
 }
 DEFAULT_WORKLOAD = "orca12-fp64"
 
@@ -128,16 +132,20 @@ def _record_iterations():
         return {}
 
 
-def oracle_sample(wl_name, wl, grid, seconds_target=15.0):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
-    setup (assembly + factor) untimed, then a run of whole oracle PCG
-    iterations; solves/s extrapolated with the oracle's own iteration count
-    for this workload (recorded by oracle/record_iterations.py)."""
+def oracle_prepare(wl, grid):
+    """Oracle setup for a workload: assembly and factor (untimed, like the GPU's)."""
     import oracle
     P = oracle.OracleProblem.from_grid(grid)
     assert P.ainv(wl["pattern"], wl["tau"], wl["q"]) == oracle.OK
-    b = P.to_wet(grid.b)
-    # calibrate: a 2-iteration run, then size the sample to ~seconds_target
+    return P, P.to_wet(grid.b)
+
+
+def oracle_sample(wl_name, wl, grid, prepared, seconds_target=15.0):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    a run of whole oracle PCG iterations on the full grid; solves/s
+    extrapolated with the oracle's own iteration count for this grid and
+    preconditioner (recorded by oracle/record_iterations.py)."""
+    P, b = prepared
     t = time.perf_counter()
     P.pcg(b, rtol=0.0, max_iter=2, max_replace=0)
     t2 = time.perf_counter() - t
@@ -146,15 +154,15 @@ def oracle_sample(wl_name, wl, grid, seconds_target=15.0):
     P.pcg(b, rtol=0.0, max_iter=iters, max_replace=0)
     dt = time.perf_counter() - t
     per_iter = dt / iters
-    rec = _record_iterations().get(wl_name)
+    recs = _record_iterations()
+    rec = recs.get(wl_name) or recs.get(wl_name.replace("-mixed", "-fp64"))
     if rec is None:
-        full = P.pcg(b, rtol=wl["rtol"])
-        rec = full.iters
+        rec = P.pcg(b, rtol=wl["rtol"]).iters
     solves_per_s = 1.0 / (per_iter * rec)
     return {"value": solves_per_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{iters} serial oracle PCG iterations on the full {grid.nx}x{grid.ny} grid "
+            "sample": f"{iters} serial FP64 oracle PCG iterations on the full {grid.nx}x{grid.ny} grid "
                       f"({dt:.1f} s, incl. the initial and final residuals), scaled by the oracle's "
-                      f"{rec} iterations per solve"}
+                      f"{rec} iterations per solve at rtol {wl['rtol']:g}"}
 
 
 def run_reference(args, wl_name, wl):
@@ -162,9 +170,10 @@ def run_reference(args, wl_name, wl):
     if rank != 0:
         return 0
     grid = gridgen.make_grid(seed=gridgen.seed_for(wl["ci"]), **wl["grid"])
+    prepared = oracle_prepare(wl, grid)
     samples = []
     for step in range(args.warmup + args.steps):
-        s = oracle_sample(wl_name, wl, grid, seconds_target=args.ref_seconds)
+        s = oracle_sample(wl_name, wl, grid, prepared, seconds_target=args.ref_seconds)
         if step >= args.warmup:
             samples.append(s)
     val = statistics.median([s["value"] for s in samples])
@@ -207,6 +216,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inner-rtol", type=float, default=0.0)
+    ap.add_argument("--tile-x", type=int, default=0)
+    ap.add_argument("--tile-y", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     wl = WORKLOADS[args.workload]
@@ -231,11 +243,12 @@ def main():
     # each rank solves its own replica of the workload (independent problems)
     grid = gridgen.make_grid(seed=gridgen.seed_for(wl["ci"]), **wl["grid"])
     t = time.perf_counter()
-    h = pcg.ainv_setup_grid(grid, pattern=wl["pattern"], drop_tol=wl["tau"], band_q=wl["q"])
+    h = pcg.ainv_setup_grid(grid, pattern=wl["pattern"], drop_tol=wl["tau"], band_q=wl["q"], tile_x=args.tile_x,
+                            tile_y=args.tile_y)
     setup_s = time.perf_counter() - t
     n_wet = h.n_wet
     zbar = _z_offdiag_per_wet(pcg, h)
-    opts = pcg.make_opts(rtol=wl["rtol"], max_iter=5000, prec=wl["prec"])
+    opts = pcg.make_opts(rtol=wl["rtol"], max_iter=5000, prec=wl["prec"], inner_rtol=args.inner_rtol)
     stream = torch.cuda.current_stream()
     b = torch.from_numpy(grid.b).cuda()
     x = torch.zeros_like(b)
@@ -293,15 +306,18 @@ def main():
     vec_bytes = grid.nx * grid.ny * 8
 
     # per-kernel roofline, live: mean event-timed duration of each kernel launch
-    ms_k1, ms_k2 = pcg.pcg_profile_kernels(h, b, iters=20)
-    w = 8
+    mixed = wl["prec"] == 1
+    ms_k1, ms_k2 = pcg.pcg_profile_kernels(h, b, iters=20, prec=wl["prec"])
+    w = 4 if mixed else 8
     bytes_k1 = n_wet * w * 9                   # read s, d, x, a, c_e, c_n; write d, x, q
     bytes_k2 = n_wet * w * (5 + zbar)          # read r, q, Z, D^-1; write r, s
     flops_k1 = n_wet * 15.0                    # d (1 FMA), x (1 FMA), A d (1 mul + 4 FMA), d.q (1 FMA)
     flops_k2 = n_wet * (4 * zbar + 7)          # r (1 FMA), Z^T (zbar FMA + 1 mul), Z (zbar FMA), 2 dots
+    fp64_flops_k1 = flops_k1 if not mixed else n_wet * 2.0          # binary32 kernels: only the dot in binary64
+    fp64_flops_k2 = flops_k2 if not mixed else n_wet * 4.0
     hbm_peak, peak_kind = _peaks()
     dom = "k_precond" if ms_k2 >= ms_k1 else "k_stencil"
-    ms_dom, by, fl = (ms_k2, bytes_k2, flops_k2) if dom == "k_precond" else (ms_k1, bytes_k1, flops_k1)
+    ms_dom, by, fl = (ms_k2, bytes_k2, fp64_flops_k2) if dom == "k_precond" else (ms_k1, bytes_k1, fp64_flops_k1)
     gbs = by / (ms_dom * 1e-3) / 1e9
     tflops = fl / (ms_dom * 1e-3) / 1e12
     t_hbm = by / (hbm_peak * 1e9)
@@ -317,7 +333,7 @@ def main():
     else:
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "traffic": traffic, "peak_kind": peak_kind}
-    roof.update({"kernel": dom, "ms_per_launch": ms_dom,
+    roof.update({"kernel": dom + ("<float>" if mixed else "<double>"), "ms_per_launch": ms_dom,
                  "per_iteration": {"ms_stencil": ms_k1, "ms_precond": ms_k2,
                                    "alg_bytes": bytes_k1 + bytes_k2,
                                    "alg_gbs": (bytes_k1 + bytes_k2) / ((ms_k1 + ms_k2) * 1e-3) / 1e9,
@@ -325,17 +341,19 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_sample(args.workload, wl, grid)
+        cpu = oracle_sample(args.workload, wl, grid, oracle_prepare(wl, grid))
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32+f64" if wl["prec"] == 1 else "f64", "data": "synthetic",
             "config": {"workload": args.workload, "grid": f"{grid.nx}x{grid.ny}", "n_wet": n_wet,
                        "pattern": {0: "tril(A)", 1: "tril(A^2)", 3: "band(T)", 4: "diag"}[wl["pattern"]],
                        "drop_tol": wl["tau"], "z_offdiag_per_wet": zbar, "rtol": wl["rtol"],
-                       "iters_per_solve": iters, "worst_true_relres": worst_true, "setup_s": setup_s,
+                       "iters_per_solve": iters, "outer_per_solve": st.outer_iters,
+                       "precision": "binary32 inner / binary64 refinement" if wl["prec"] == 1 else "binary64",
+                       "worst_true_relres": worst_true, "setup_s": setup_s,
                        "l2": "inputs larger than L2 (working set ~%.2f GB vs 126 MB L2)"
                              % (n_wet * 8 * (14 + zbar) / 1e9),
                        "parallelism": f"replicas x{world}"},

@@ -174,7 +174,7 @@ int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream);
  * synchronises cuda_stream before returning. Errors: PCG_EINVAL, PCG_ECUDA. */
 int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void *cuda_stream);
 
-/* s = Z D^-1 Z^T r on the device kernels of the iteration (Algorithm 1, line 7). */
+/* s = Z D^-1 Z^T r on the device kernels of the iteration (the preconditioning step of Algorithm 1). */
 int pcg_precond_apply(pcg_handle *h, const double *r, double *s, void *cuda_stream);
 
 /* Export the library's own factor for comparison: for each wet point k in
@@ -203,11 +203,13 @@ int pcg_debug_wait_timeout(pcg_handle *h, int32_t unit, double timeout_ms, void 
 /* Measurement entry point: loads b, runs the init kernels, then `iters` PCG
  * iterations as individual launches of the stencil kernel and of the
  * preconditioner kernel, each bracketed by CUDA events on cuda_stream.
- * Writes the mean duration of one launch of each (milliseconds). The
- * iterations are real (the state advances as in pcg_solve); x is not
- * returned. Errors: PCG_EINVAL, PCG_ECUDA. */
-int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, double *ms_stencil, double *ms_precond,
-                        void *cuda_stream);
+ * Writes the mean duration of one launch of each (milliseconds). prec =
+ * PCG_FP64 times the binary64 kernels; PCG_MIXED times the binary32 kernels of
+ * the inner solves (on b rounded to binary32). The iterations are real (the
+ * state advances as in a solve); x is not returned. Errors: PCG_EINVAL,
+ * PCG_ECUDA. */
+int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, int32_t prec, double *ms_stencil,
+                        double *ms_precond, void *cuda_stream);
 
 /* Number of kernel launches this library has issued since it was loaded,
  * counting every kernel run inside a loop graph. */

@@ -96,7 +96,7 @@ def _load():
         "pcg_status_string": (C.c_char_p, [C.c_int]),
         "pcg_last_error_message": (C.c_char_p, []),
         "pcg_debug_wait_timeout": (C.c_int, [vp, i32, dbl, vp]),
-        "pcg_profile_kernels": (C.c_int, [vp, vp, i32, C.POINTER(dbl), C.POINTER(dbl), vp]),
+        "pcg_profile_kernels": (C.c_int, [vp, vp, i32, i32, C.POINTER(dbl), C.POINTER(dbl), vp]),
         "pcg_kernel_launches": (C.c_uint64, []),
         "solver_server_create": (C.c_int, [C.POINTER(pcg_server_opts), C.POINTER(vp)]),
         "solver_server_register": (C.c_int, [vp, vp, C.POINTER(i32)]),
@@ -283,10 +283,10 @@ def pcg_debug_wait_timeout(h: Handle, unit=0, timeout_ms=50.0, stream=None) -> i
     return int(lib.pcg_debug_wait_timeout(h.ptr, int(unit), float(timeout_ms), _stream(stream)))
 
 
-def pcg_profile_kernels(h: Handle, b, iters=20, stream=None):
+def pcg_profile_kernels(h: Handle, b, iters=20, prec=PCG_FP64, stream=None):
     """Mean duration (ms) of one stencil launch and one preconditioner launch."""
     a, c = C.c_double(), C.c_double()
-    rc = lib.pcg_profile_kernels(h.ptr, _ptr(b), int(iters), C.byref(a), C.byref(c), _stream(stream))
+    rc = lib.pcg_profile_kernels(h.ptr, _ptr(b), int(iters), int(prec), C.byref(a), C.byref(c), _stream(stream))
     if rc != PCG_OK:
         raise PCGError(rc, "pcg_profile_kernels")
     return a.value, c.value

@@ -34,6 +34,7 @@ static KernelSet make_set() {
   k.smem1 = K1Geom<T, TX>::SMEM;
   k.smem2 = K2Geom<T, TX, P>::SMEM;
   k.tx = TX;
+  k.tb = TX + 32;
   k.ok = true;
   return k;
 }
@@ -233,7 +234,7 @@ static int build_loop_graph(LoopPlan &L) {
       cudaKernelNodeParams kp{};
       kp.func = const_cast<void *>(pass == 0 ? G.ks.k1 : G.ks.k2);
       kp.gridDim = dim3(G.n_units);
-      kp.blockDim = dim3(G.ks.tx);
+      kp.blockDim = dim3(G.ks.tb);
       kp.sharedMemBytes = (unsigned)(pass == 0 ? G.ks.smem1 : G.ks.smem2);
       kp.kernelParams = args;
       cudaGraphNode_t node;
@@ -289,7 +290,7 @@ int members_loop(LoopPlan &L, LaunchState *ls_host, int max_launches, cudaStream
           if (G.n_units <= 0) continue;
           const int guard = (pass == 0 && !guarded) ? 1 : 0;
           guarded = guarded || guard;
-          int rc = launch(pass == 0 ? G.ks.k1 : G.ks.k2, G.n_units, G.ks.tx, pass == 0 ? G.ks.smem1 : G.ks.smem2,
+          int rc = launch(pass == 0 ? G.ks.k1 : G.ks.k2, G.n_units, G.ks.tb, pass == 0 ? G.ks.smem1 : G.ks.smem2,
                           kparams(L, G, pass == 0 ? (int)K1_ITER : (int)K2_ITER, 0, guard), s);
           if (rc) return rc;
         }
@@ -357,35 +358,37 @@ int plan_single(pcg_handle *h) {
 }
 
 // Plan over several grids: members grouped by kernel set.
-int plan_build(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls, cudaStream_t s) {
+template <typename T>
+static int plan_build_t(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls,
+                        DevPlanes<T> pcg_handle::*planes, cudaStream_t s) {
   L.ls = ls;
   std::vector<std::vector<int>> groups;
   for (int i = 0; i < n; ++i) {
     bool placed = false;
     for (auto &g : groups)
-      if (hs[g[0]]->p64.ks.k2 == hs[i]->p64.ks.k2 && hs[g[0]]->p64.ks.k1 == hs[i]->p64.ks.k1) {
+      if ((hs[g[0]]->*planes).ks.k2 == (hs[i]->*planes).ks.k2 && (hs[g[0]]->*planes).ks.k1 == (hs[i]->*planes).ks.k1) {
         g.push_back(i); placed = true; break;
       }
     if (!placed) groups.push_back({i});
   }
   for (auto &g : groups) {
-    std::vector<GridDev<double>> gds;
+    std::vector<GridDev<T>> gds;
     std::vector<Unit> units;
     for (size_t mi = 0; mi < g.size(); ++mi) {
-      auto &P = hs[g[mi]]->p64;
+      auto &P = hs[g[mi]]->*planes;
       gds.push_back(P.gd);
       for (Unit u : P.units) { u.g = (int16_t)mi; units.push_back(u); }
     }
     void *gd_dev = nullptr, *un_dev = nullptr;
-    CK(cudaMalloc(&gd_dev, sizeof(GridDev<double>) * gds.size()));
+    CK(cudaMalloc(&gd_dev, sizeof(GridDev<T>) * gds.size()));
     L.owned.push_back(gd_dev);
     CK(cudaMalloc(&un_dev, sizeof(Unit) * std::max<size_t>(units.size(), 1)));
     L.owned.push_back(un_dev);
-    CK(cudaMemcpyAsync(gd_dev, gds.data(), sizeof(GridDev<double>) * gds.size(), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(gd_dev, gds.data(), sizeof(GridDev<T>) * gds.size(), cudaMemcpyHostToDevice, s));
     if (!units.empty()) CK(cudaMemcpyAsync(un_dev, units.data(), sizeof(Unit) * units.size(), cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));   // the host vectors above go out of scope
     PlanGroup pg;
-    pg.ks = hs[g[0]]->p64.ks;
+    pg.ks = (hs[g[0]]->*planes).ks;
     pg.n_units = (int)units.size();
     pg.gd_dev = gd_dev;
     pg.units_dev = (const Unit *)un_dev;
@@ -393,6 +396,40 @@ int plan_build(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, Launc
   }
   if (with_graph && build_loop_graph(L) != PCG_OK) L.graph_ok = false;
   g_err.clear();
+  return PCG_OK;
+}
+
+int plan_build(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls, cudaStream_t s) {
+  return plan_build_t<double>(L, hs, n, with_graph, ls, &pcg_handle::p64, s);
+}
+
+int plan_build32(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls, cudaStream_t s) {
+  return plan_build_t<float>(L, hs, n, with_graph, ls, &pcg_handle::p32, s);
+}
+
+// The binary32 planes of a handle (coefficients, Z and D^-1 rounded to
+// binary32; same strips and units as the binary64 planes) and their loop plan.
+int ensure_f32(pcg_handle *h, cudaStream_t s) {
+  if (h->plan32) return PCG_OK;
+  int rc = upload_planes<float>(h, h->p32, s);
+  if (rc) { h->p32.release(); return rc; }
+  if (!h->st32_host && cudaMallocHost(&h->st32_host, sizeof(SolveState)) != cudaSuccess) {
+    cudaGetLastError(); set_error("pinned allocation failed"); return PCG_ENOMEM;
+  }
+  h->bytes += h->p32.bytes;
+  pcg_handle *hs[1] = {h};
+  auto L = std::make_unique<LoopPlan>();
+  L->ls = h->ls;
+  PlanGroup g;
+  g.ks = h->p32.ks;
+  g.n_units = h->p32.n_units;
+  g.gd_dev = h->p32.gd_dev;
+  g.units_dev = h->p32.units_dev;
+  L->groups.push_back(g);
+  if (build_loop_graph(*L) != PCG_OK) L->graph_ok = false;
+  g_err.clear();
+  (void)hs;
+  h->plan32 = std::move(L);
   return PCG_OK;
 }
 
@@ -435,9 +472,9 @@ int member_load(Member &m, const pcg_opts &o, bool pack_x0, cudaStream_t s) {
 int members_init(LoopPlan &L, cudaStream_t s) {
   int rc;
   for (auto &G : L.groups)
-    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tx, G.ks.smem1, kparams(L, G, K1_RESID_INIT, 0, 0), s))) return rc;
+    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tb, G.ks.smem1, kparams(L, G, K1_RESID_INIT, 0, 0), s))) return rc;
   for (auto &G : L.groups)
-    if ((rc = launch(G.ks.k2, G.n_units, G.ks.tx, G.ks.smem2, kparams(L, G, K2_INIT, 0, 0), s))) return rc;
+    if ((rc = launch(G.ks.k2, G.n_units, G.ks.tb, G.ks.smem2, kparams(L, G, K2_INIT, 0, 0), s))) return rc;
   return PCG_OK;
 }
 
@@ -446,7 +483,7 @@ int members_close(LoopPlan &L, cudaStream_t s) {
   for (auto &G : L.groups)
     if ((rc = launch(G.ks.fin, G.n_units, G.ks.tx, 0, kparams(L, G, 0, 0, 0), s))) return rc;
   for (auto &G : L.groups)
-    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tx, G.ks.smem1, kparams(L, G, K1_RESID_CHECK, 0, 0), s))) return rc;
+    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tb, G.ks.smem1, kparams(L, G, K1_RESID_CHECK, 0, 0), s))) return rc;
   return PCG_OK;
 }
 
@@ -530,6 +567,120 @@ static int solve_members64(LoopPlan &L, LaunchState *ls_host, std::vector<Member
   return PCG_OK;
 }
 
+// Mixed precision: iterative refinement in binary64 around binary32 PCG
+// solves. Each outer step computes the binary64 residual r = b - A x (the
+// binary64 stencil kernel), stops if ||r|| / ||b|| <= rtol, otherwise solves
+// A e = r in binary32 (r scaled by a power of two, inner tolerance
+// inner_rtol, dot products accumulated in binary64) and updates x += e in
+// binary64.
+int solve_members_mixed(LoopPlan &L64, LoopPlan &L32, LaunchState *ls_host, std::vector<Member> &M,
+                        const pcg_opts &o, cudaStream_t s) {
+  int rc;
+  for (auto &m : M) {
+    if ((rc = member_load(m, o, true, s))) return rc;
+    m.inner_iters = 0; m.inner_solves = 0; m.relres64 = 0.0;
+  }
+  int budget_default = 0;
+  for (auto &m : M) budget_default = std::max(budget_default, std::max(m.h->G.n, 1));
+  const int budget = o.max_iter > 0 ? o.max_iter : budget_default;
+  for (int outer = 0;; ++outer) {
+    int remaining = 0;
+    for (auto &m : M) remaining += m.final_status < 0 ? 1 : 0;
+    if (remaining == 0) break;
+    // binary64 residual of every unfinished grid
+    if ((rc = members_arm(L64, ls_host, remaining, 1, s))) return rc;
+    for (auto &G : L64.groups)
+      if ((rc = launch(G.ks.k1, G.n_units, G.ks.tb, G.ks.smem1, kparams(L64, G, K1_RESID_INIT, 0, 0), s))) return rc;
+    for (auto &m : M) CK(cudaMemcpyAsync(m.st_host, m.h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int inner = 0;
+    for (auto &m : M) {
+      auto &P32 = m.h->p32;
+      SolveState st32{};
+      st32.status = PCG_OK; st32.done = 1; st32.retired = 1;
+      if (m.final_status < 0) {
+        SolveState &st = *m.st_host;
+        int fs = -1;
+        if (st.status != PCG_OK) fs = st.status;
+        else if (st.bzero) {
+          CK(cudaMemsetAsync(m.h->p64.plane_start(m.h->p64.vec(0)), 0, m.h->p64.plane_elems * sizeof(double), s));
+          m.relres64 = 0.0;
+          fs = PCG_OK;
+        } else {
+          m.relres64 = std::sqrt(st.rr) / std::sqrt(st.bb);
+          if (!(m.relres64 > o.rtol)) fs = PCG_OK;
+          else if (!std::isfinite(m.relres64)) fs = PCG_EBREAKDOWN;
+          else if (outer >= o.max_outer || m.inner_iters >= budget) fs = PCG_ENOTCONV;
+        }
+        if (fs >= 0) {
+          m.final_status = fs;
+          st.retired = 1; st.done = 1;
+          CK(cudaMemcpyAsync(&m.h->p64.st->done, &st.done, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+          CK(cudaMemcpyAsync(&m.h->p64.st->retired, &st.retired, sizeof(int32_t), cudaMemcpyHostToDevice, s));
+        } else {
+          // right-hand side of the inner solve: r scaled to unit root-mean-square
+          const double rms = std::sqrt(st.rr / std::max(m.h->G.n, 1));
+          m.scale = std::ldexp(1.0, -std::ilogb(rms > 0 ? rms : 1.0));
+          const GridDev<double> *g64 = m.h->p64.gd_dev;
+          const GridDev<float> *g32 = P32.gd_dev;
+          const Unit *un = m.h->p64.units_dev;
+          double sc = m.scale;
+          void *args[] = {(void *)&g64, (void *)&g32, (void *)&un, &sc};
+          const void *f = m.h->tx == 128 ? (const void *)k_residual_to_f32<128> : (const void *)k_residual_to_f32<64>;
+          if (m.h->p64.n_units > 0) CK(cudaLaunchKernel(f, dim3(m.h->p64.n_units), dim3(m.h->tx), args, 0, s));
+          CK(cudaMemsetAsync(P32.plane_start(P32.vec(0)), 0, P32.plane_elems * sizeof(float), s));
+          for (int v : {5, 6}) CK(cudaMemsetAsync(P32.plane_start(P32.vec(v)), 0, P32.plane_elems * sizeof(float), s));
+          st32.rtol = o.inner_rtol;
+          st32.max_iter = std::max(1, budget - m.inner_iters);
+          st32.done = 0; st32.retired = 0;
+          ++inner;
+        }
+      }
+      *m.h->st32_host = st32;
+      CK(cudaMemcpyAsync(P32.st, m.h->st32_host, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+    }
+    if (inner == 0) continue;
+    // binary32 inner solves of all of them together
+    if ((rc = members_arm(L32, ls_host, inner, budget + 64, s))) return rc;
+    if ((rc = members_init(L32, s))) return rc;
+    if ((rc = members_loop(L32, ls_host, budget + 64, s))) return rc;
+    for (auto &G : L32.groups)
+      if ((rc = launch(G.ks.fin, G.n_units, G.ks.tx, 0, kparams(L32, G, 0, 0, 0), s))) return rc;
+    for (auto &m : M) CK(cudaMemcpyAsync(m.h->st32_host, m.h->p32.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ls_host, L32.ls, sizeof(LaunchState), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (L32.graph_ok) g_launches.fetch_add((uint64_t)std::max(ls_host->launches, 0) * L32.body_kernels, std::memory_order_relaxed);
+    for (auto &m : M) {
+      if (m.final_status >= 0) continue;
+      const SolveState &st32 = *m.h->st32_host;
+      if (st32.retired) continue;
+      m.inner_iters += st32.iter;
+      m.inner_solves += 1;
+      if (st32.status == PCG_EBREAKDOWN && st32.iter == 0) { m.final_status = PCG_EBREAKDOWN; continue; }
+      // x += e / scale in binary64
+      const GridDev<double> *g64 = m.h->p64.gd_dev;
+      const GridDev<float> *g32 = m.h->p32.gd_dev;
+      const Unit *un = m.h->p64.units_dev;
+      double inv = 1.0 / m.scale;
+      void *args[] = {(void *)&g64, (void *)&g32, (void *)&un, &inv};
+      const void *f = m.h->tx == 128 ? (const void *)k_correct_f64<128> : (const void *)k_correct_f64<64>;
+      if (m.h->p64.n_units > 0) CK(cudaLaunchKernel(f, dim3(m.h->p64.n_units), dim3(m.h->tx), args, 0, s));
+    }
+  }
+  for (auto &m : M) if ((rc = member_store(m, s))) return rc;
+  CK(cudaStreamSynchronize(s));
+  for (auto &m : M) {
+    if (!m.stats) continue;
+    m.stats->iters = m.inner_iters;
+    m.stats->outer_iters = m.inner_solves;
+    m.stats->status = m.final_status;
+    m.stats->replacements = 0;
+    m.stats->relres = m.relres64;
+    m.stats->true_relres = m.relres64;
+  }
+  return PCG_OK;
+}
+
 std::string status_name(int s) {
   switch (s) {
     case PCG_OK: return "ok";
@@ -555,7 +706,7 @@ static int choose_ty(int nx, int ny, int tx) {
   const int ntx = (nx + tx - 1) / tx;
   // aim at >= ~4 CTAs per SM of 148 when the grid allows it, rows 8..32
   int ty = (int)std::floor((double)ntx * ny / (148.0 * 4));
-  return std::max(8, std::min(32, ty));
+  return std::max(8, std::min(64, ty));
 }
 
 }  // namespace pcg
@@ -687,7 +838,7 @@ int pcg_solve_batched(pcg_handle *const *hs, int32_t nbatch, const double *const
   }
   pcg_opts o;
   fill_opts(opts, o);
-  if (o.prec == PCG_MIXED) { set_error("mixed precision is not built into this library"); return PCG_EINVAL; }
+  if (o.prec != PCG_FP64 && o.prec != PCG_MIXED) { set_error("unknown precision"); return PCG_EINVAL; }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   std::vector<Member> M(nbatch);
   for (int i = 0; i < nbatch; ++i) {
@@ -695,7 +846,20 @@ int pcg_solve_batched(pcg_handle *const *hs, int32_t nbatch, const double *const
     M[i].st_host = hs[i]->st_host;
   }
   int rc;
-  if (nbatch == 1) {
+  if (o.prec == PCG_MIXED) {
+    for (int i = 0; i < nbatch; ++i)
+      if ((rc = ensure_f32(hs[i], s))) return rc;
+    if (nbatch == 1) {
+      if ((rc = plan_single(hs[0]))) return rc;
+      rc = solve_members_mixed(*hs[0]->plan64, *hs[0]->plan32, hs[0]->ls_host, M, o, s);
+    } else {
+      LoopPlan L64, L32;
+      if ((rc = plan_build(L64, hs, nbatch, false, hs[0]->ls, s))) return rc;
+      if ((rc = plan_build32(L32, hs, nbatch, true, hs[0]->ls, s))) return rc;
+      rc = solve_members_mixed(L64, L32, hs[0]->ls_host, M, o, s);
+      cudaStreamSynchronize(s);
+    }
+  } else if (nbatch == 1) {
     if ((rc = plan_single(hs[0]))) return rc;
     rc = solve_members64(*hs[0]->plan64, hs[0]->ls_host, M, o, s);
   } else {
@@ -724,7 +888,7 @@ int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream) {
   KParams p{};
   p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K1_SPMV; p.dbg_skip_unit = -1;
   p.timeout_ns = default_timeout_ns();
-  if ((rc = launch(P.ks.k1, P.n_units, P.tx, P.ks.smem1, p, s))) return rc;
+  if ((rc = launch(P.ks.k1, P.n_units, P.ks.tb, P.ks.smem1, p, s))) return rc;
   if ((rc = unpack_user(h, q, 2, s))) return rc;
   CK(cudaStreamSynchronize(s));
   return PCG_OK;
@@ -739,46 +903,65 @@ int pcg_precond_apply(pcg_handle *h, const double *r, double *sv, void *cuda_str
   KParams p{};
   p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K2_APPLY; p.dbg_skip_unit = -1;
   p.timeout_ns = default_timeout_ns();
-  if ((rc = launch(P.ks.k2, P.n_units, P.tx, P.ks.smem2, p, s))) return rc;
+  if ((rc = launch(P.ks.k2, P.n_units, P.ks.tb, P.ks.smem2, p, s))) return rc;
   if ((rc = unpack_user(h, sv, 1, s))) return rc;
   CK(cudaStreamSynchronize(s));
   return PCG_OK;
 }
 
-int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, double *ms_stencil, double *ms_precond,
-                        void *cuda_stream) {
-  if (!h || !b || iters <= 0) { set_error("invalid arguments"); return PCG_EINVAL; }
+int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, int32_t prec, double *ms_stencil,
+                        double *ms_precond, void *cuda_stream) {
+  if (!h || !b || iters <= 0 || (prec != PCG_FP64 && prec != PCG_MIXED)) { set_error("invalid arguments"); return PCG_EINVAL; }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int rc;
   if ((rc = plan_single(h))) return rc;
-  LoopPlan &L = *h->plan64;
+  if (prec == PCG_MIXED && (rc = ensure_f32(h, s))) return rc;
   pcg_opts o;
   fill_opts(nullptr, o);
   o.rtol = 0.0;                       // iterate the requested number of times
   o.max_iter = iters + 1;
-  std::vector<Member> M(1);
-  M[0].h = h; M[0].b = b; M[0].x = h->stage; M[0].st_host = h->st_host;
-  M[0].x = nullptr;
-  pcg_opts lo = o;
-  lo.use_x0 = 0;
-  {
-    // member_load packs b and zeroes x (no x0)
-    Member &m = M[0];
-    double *dummy = nullptr;
-    m.x = dummy;
-    if ((rc = member_load(m, lo, false, s))) return rc;
+  o.use_x0 = 0;
+  Member m;
+  m.h = h; m.b = b; m.x = nullptr; m.st_host = h->st_host;
+  if ((rc = member_load(m, o, false, s))) return rc;   // packs b, zeroes x
+  LoopPlan *L = h->plan64.get();
+  SolveState *st_dev = h->p64.st;
+  SolveState *st_host = h->st_host;
+  if (prec == PCG_MIXED) {
+    // the binary32 system with right-hand side b (scale 1)
+    const GridDev<double> *g64 = h->p64.gd_dev;
+    const GridDev<float> *g32 = h->p32.gd_dev;
+    const Unit *un = h->p64.units_dev;
+    // b64 -> r64 plane 0 by a residual pass with x = 0, then to binary32
+    if ((rc = members_arm(*L, h->ls_host, 1, 1, s))) return rc;
+    const PlanGroup &G64 = L->groups[0];
+    if ((rc = launch(G64.ks.k1, G64.n_units, G64.ks.tb, G64.ks.smem1, kparams(*L, G64, K1_RESID_INIT, 0, 0), s))) return rc;
+    double sc = 1.0;
+    void *args[] = {(void *)&g64, (void *)&g32, (void *)&un, &sc};
+    const void *f = h->tx == 128 ? (const void *)k_residual_to_f32<128> : (const void *)k_residual_to_f32<64>;
+    if (h->p64.n_units > 0) CK(cudaLaunchKernel(f, dim3(h->p64.n_units), dim3(h->tx), args, 0, s));
+    auto &P32 = h->p32;
+    CK(cudaMemsetAsync(P32.plane_start(P32.vec(0)), 0, P32.plane_elems * sizeof(float), s));
+    for (int v : {5, 6}) CK(cudaMemsetAsync(P32.plane_start(P32.vec(v)), 0, P32.plane_elems * sizeof(float), s));
+    SolveState st32{};
+    st32.status = PCG_OK; st32.rtol = 0.0; st32.max_iter = iters + 1;
+    *h->st32_host = st32;
+    CK(cudaMemcpyAsync(P32.st, h->st32_host, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+    L = h->plan32.get();
+    st_dev = P32.st;
+    st_host = h->st32_host;
   }
-  if ((rc = members_arm(L, h->ls_host, 1, iters + 8, s))) return rc;
-  if ((rc = members_init(L, s))) return rc;
-  const PlanGroup &G = L.groups[0];
+  if ((rc = members_arm(*L, h->ls_host, 1, iters + 8, s))) return rc;
+  if ((rc = members_init(*L, s))) return rc;
+  const PlanGroup &G = L->groups[0];
   std::vector<cudaEvent_t> ev(4 * iters);
   for (auto &e : ev) CK(cudaEventCreate(&e));
   for (int it = 0; it < iters; ++it) {
     CK(cudaEventRecord(ev[4 * it], s));
-    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tx, G.ks.smem1, kparams(L, G, K1_ITER, 0, 0), s))) return rc;
+    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tb, G.ks.smem1, kparams(*L, G, K1_ITER, 0, 0), s))) return rc;
     CK(cudaEventRecord(ev[4 * it + 1], s));
     CK(cudaEventRecord(ev[4 * it + 2], s));
-    if ((rc = launch(G.ks.k2, G.n_units, G.ks.tx, G.ks.smem2, kparams(L, G, K2_ITER, 0, 0), s))) return rc;
+    if ((rc = launch(G.ks.k2, G.n_units, G.ks.tb, G.ks.smem2, kparams(*L, G, K2_ITER, 0, 0), s))) return rc;
     CK(cudaEventRecord(ev[4 * it + 3], s));
   }
   CK(cudaStreamSynchronize(s));
@@ -790,9 +973,9 @@ int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, double *m
     t1 += a; t2 += c;
   }
   for (auto &e : ev) cudaEventDestroy(e);
-  CK(cudaMemcpyAsync(h->st_host, h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(st_host, st_dev, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (h->st_host->done && h->st_host->iter < iters) {
+  if (st_host->done && st_host->iter < iters) {
     set_error("the iteration stopped early (converged or broke down) while profiling");
     return PCG_EINVAL;
   }
@@ -817,7 +1000,10 @@ int32_t pcg_n_wet(const pcg_handle *h) { return h ? h->G.n : 0; }
 void pcg_free(pcg_handle *h) {
   if (!h) return;
   h->plan64.reset();
+  h->plan32.reset();
   h->p64.release();
+  h->p32.release();
+  cudaFreeHost(h->st32_host);
   cudaFree(h->ls);
   cudaFree(h->stage);
   cudaFreeHost(h->ls_host);
@@ -843,7 +1029,7 @@ int pcg_debug_wait_timeout(pcg_handle *h, int32_t unit, double timeout_ms, void 
   p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K2_INIT;
   p.dbg_skip_unit = unit;
   p.timeout_ns = (uint64_t)(timeout_ms * 1e6);
-  int rc = launch(P.ks.k2, P.n_units, P.tx, P.ks.smem2, p, s);
+  int rc = launch(P.ks.k2, P.n_units, P.ks.tb, P.ks.smem2, p, s);
   if (rc) return rc;
   CK(cudaMemcpyAsync(h->st_host, P.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

@@ -24,7 +24,8 @@ namespace pcg {
 struct KernelSet {
   const void *k1 = nullptr, *k2 = nullptr, *fin = nullptr, *pack = nullptr, *unpack = nullptr;
   size_t smem1 = 0, smem2 = 0;
-  int tx = 0;
+  int tx = 0;        // strip width: threads of the small kernels
+  int tb = 0;        // threads of the stencil and preconditioner kernels (tx + a producer warp)
   bool ok = false;
 };
 
@@ -88,11 +89,14 @@ struct pcg_handle {
   double tau = 0.0;
   int tx = 0, ty = 0;
   pcg::DevPlanes<double> p64;
+  pcg::DevPlanes<float> p32;              // binary32 copies for the mixed-precision inner solves (lazy)
+  pcg::SolveState *st32_host = nullptr;   // pinned mirror of p32's state
   pcg::LaunchState *ls = nullptr;        // device
   pcg::LaunchState *ls_host = nullptr;   // pinned
   pcg::SolveState *st_host = nullptr;    // pinned mirror
   double *stage = nullptr;               // device [ny][nx] staging for host buffers
   std::unique_ptr<pcg::LoopPlan> plan64;
+  std::unique_ptr<pcg::LoopPlan> plan32;
   size_t bytes = 0;
 };
 
@@ -107,6 +111,10 @@ struct Member {
   SolveState *st_host = nullptr;
   int replacements = 0;
   int final_status = -1;
+  // mixed precision bookkeeping
+  int inner_iters = 0, inner_solves = 0;
+  double relres64 = 0.0;
+  double scale = 1.0;
 };
 
 // phases of a solve, shared by pcg_solve_batched and the solver server
@@ -121,6 +129,10 @@ bool member_decide(Member &m, const pcg_opts &o, bool overrun, cudaStream_t s, i
 int member_store(Member &m, cudaStream_t s);                                      // unpack x
 void member_stats(Member &m);
 int plan_single(pcg_handle *h);                                                   // h->plan64
+int ensure_f32(pcg_handle *h, cudaStream_t s);                                     // h->p32, h->plan32
+int plan_build32(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls, cudaStream_t s);
+int solve_members_mixed(LoopPlan &L64, LoopPlan &L32, LaunchState *ls_host, std::vector<Member> &M,
+                        const pcg_opts &o, cudaStream_t s);
 int plan_build(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls, cudaStream_t s);
 std::string status_name(int s);
 void fill_opts(const pcg_opts *o, pcg_opts &out);

@@ -106,6 +106,22 @@ struct Pat<PCG_PAT_BAND_T, Q> {
 
 __host__ __device__ constexpr int round_up_c(int v, int a) { return (v + a - 1) / a * a; }
 
+// Exact widening to binary64 for the dot-product accumulators. For binary32
+// values it assembles the binary64 bit pattern from the binary32 fields with
+// integer operations (IEEE 754: sign kept, exponent re-biased by 1023 - 127,
+// 23-bit fraction shifted into the top of the 52-bit fraction), so the
+// accumulation in binary64 costs no conversion on the slow FP64 pipe of this
+// GPU. Zero, subnormal, infinite and NaN inputs take the hardware conversion.
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) {
+  const uint32_t u = __float_as_uint(v);
+  const uint32_t e = (u >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) return (double)v;
+  const uint32_t hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u & 0x7FFFFFu) >> 3);
+  const uint32_t lo = (u & 0x7u) << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
+
 // ------------------------------------------------------------ stores
 // Store one value of column `col` (0 <= col < nx) of a row, together with its
 // periodic copies in the ghost columns.
@@ -180,12 +196,91 @@ __device__ __forceinline__ void grid_finished(SolveState *st, LaunchState *ls, i
 
 __device__ __forceinline__ void flag_timeout(SolveState *st) { atomicCAS(&st->status, PCG_OK, PCG_ETIMEOUT); }
 
+// ------------------------------------------------------------ row streaming
+// A CTA is TX compute threads plus one producer warp. The producer streams
+// rows: lane a owns field a of a row (source plane, place in a ring slot,
+// size) and issues its bulk copy (cp.async.bulk) into the slot; lane 0 first
+// arms the slot's "full" mbarrier with the row's byte count. A bulk copy
+// occupies its issuing thread for several hundred ns on this GPU, so the
+// producer runs ahead on its own and the compute threads never wait for an
+// issue, only for data. When the compute threads are done with a row, one of
+// them arrives on the slot's "empty" mbarrier; the producer waits for that
+// before it refills the slot.
+struct RowCopy {
+  const char *src;             // element (i0 - halo, row 0) of the plane, as bytes
+  uint32_t dst;                // byte offset inside a ring slot
+  uint32_t bytes;
+  int when;                    // 0: every streamed row; 1: rows < mhi; 2: rows in [j0, mhi); 3: rows >= j0
+};
+
+__device__ __forceinline__ bool row_wanted(int when, int m, int j0, int mhi) {
+  switch (when) {
+    case 1: return m < mhi;
+    case 2: return m >= j0 && m < mhi;
+    case 3: return m >= j0;
+    default: return true;
+  }
+}
+
+// Issue row m into its slot (producer warp, all lanes).
+__device__ __forceinline__ void issue_row(const RowCopy &c, unsigned char *slot_base, uint64_t *full, int m,
+                                          size_t pitch_bytes, int j0, int mhi, bool skip) {
+  const bool want = c.src && row_wanted(c.when, m, j0, mhi);
+  const uint32_t total = __reduce_add_sync(0xffffffffu, want ? c.bytes : 0u);
+  if ((threadIdx.x & 31) == 0) mbar_arrive_expect_tx(full, total);
+  __syncwarp();
+  if (want && !skip) {
+    fence_proxy_async();
+    bulk_g2s(slot_base + c.dst, c.src + (ptrdiff_t)m * (ptrdiff_t)pitch_bytes, c.bytes, full);
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Barrier of the NT compute threads only (named barrier 1), with an AND vote.
+template <int NT>
+__device__ __forceinline__ bool compute_sync_and(bool v) {
+  uint32_t out;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n barrier.cta.red.and.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(out)
+      : "r"((uint32_t)v), "r"(NT)
+      : "memory");
+  return out != 0;
+}
+
+// The producer loop: rows [mlo, mhi] into NST ring slots. Slot of row n is
+// (n - mlo) % NST; its k-th fill waits for the (k-1)-th release. Returns the
+// last row issued. Bounded: a release that never comes ends the loop.
+template <int NST>
+__device__ __forceinline__ int produce_rows(const RowCopy &c, unsigned char *ring, int slot_bytes, uint64_t *full,
+                                            uint64_t *empty, int mlo, int mhi, size_t pitch_bytes, int j0,
+                                            bool skip_first, uint64_t timeout_ns, const volatile int *abort) {
+  int last = mlo - 1;
+  for (int n = mlo; n <= mhi; ++n) {
+    const int slot = (n - mlo) % NST, fill = (n - mlo) / NST;
+    if (fill > 0) {
+      bool ok = true;
+      if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(&empty[slot], (uint32_t)((fill - 1) & 1), timeout_ns);
+      ok = __shfl_sync(0xffffffffu, ok, 0) && !*abort;
+      if (!ok) break;
+    }
+    issue_row(c, ring + (size_t)slot * slot_bytes, &full[slot], n, pitch_bytes, j0, mhi, skip_first && n == mlo);
+    last = n;
+  }
+  return last;
+}
+
 // ------------------------------------------------------------ kernel 1
 // Stencil pass (Section 3, Eq. 9 in SPD form). Kinds:
 //  K1_ITER        d' = s + beta d; x += pending d; q = A d'; sum d'.q
 //  K1_RESID_INIT  r = b - A x; sums r.r and b.b
 //  K1_RESID_CHECK r = b - A x; sum r.r (true residual)
 //  K1_SPMV        q = A v (v in d[0])
+// Step m computes d' on row m, then q on row m - 2 (whose north neighbour
+// row m - 1 was finished in the previous step): one compute barrier per row.
 template <typename T, int TX>
 struct K1Geom {
   static constexpr int AL = 16 / (int)sizeof(T);     // elements per 16 bytes
@@ -193,30 +288,38 @@ struct K1Geom {
   static constexpr int WS = TX + 2 * H;              // s, d_old / x / v: [i0-H, i0+TX+H)
   static constexpr int WE = TX + H;                  // c_e: [i0-H, i0+TX)
   static constexpr int WT = TX;                      // c_n, a, x / b
-  static constexpr int NST = 6;                      // ring slots (3 live rows + 3 ahead)
+  static constexpr int PF = sizeof(T) == 8 ? 3 : 4;  // rows streamed ahead
+  static constexpr int NST = 4 + PF;                 // ring slots: rows m-3..m live
+  static constexpr int NDN = 4;                      // rows of d' kept
+  static constexpr int NT = TX + 32;                 // compute threads + producer warp
   static constexpr int OFF_S = 0, OFF_D = WS, OFF_E = 2 * WS, OFF_N = 2 * WS + WE, OFF_A = OFF_N + WT,
                        OFF_X = OFF_A + WT, SLOT = OFF_X + WT;
   static constexpr int WDN = TX + 2;                 // d' ring: [i0-1, i0+TX+1)
-  static constexpr size_t SMEM = 128 + sizeof(T) * ((size_t)NST * SLOT + 3 * WDN) + 16 * 2 * (TX / 32) + 64;
+  static constexpr size_t SMEM = 256 + sizeof(T) * ((size_t)NST * SLOT + NDN * WDN) + 16 * (NT / 32) + 64;
 };
 
 template <typename T, int TX>
-__global__ void __launch_bounds__(TX) k_stencil(KParams p) {
+__global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
   using G = K1Geom<T, TX>;
+  constexpr int NT = G::NT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
-  T *ring = reinterpret_cast<T *>(smem_raw + 128);
-  T *dn = ring + (size_t)G::NST * G::SLOT;
-  double *red = reinterpret_cast<double *>(dn + 3 * G::WDN);
-  int *flag = reinterpret_cast<int *>(red + 2 * (TX / 32));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
+  uint64_t *empty = full + G::NST;
+  volatile int *ctl = reinterpret_cast<volatile int *>(smem_raw + 224);   // abort, issued, consumed
+  unsigned char *ring_b = smem_raw + 256;
+  const T *ring = reinterpret_cast<const T *>(ring_b);
+  T *dn = reinterpret_cast<T *>(ring_b + sizeof(T) * (size_t)G::NST * G::SLOT);
+  double *red = reinterpret_cast<double *>(dn + (size_t)G::NDN * G::WDN);
+  int *flag = reinterpret_cast<int *>(red + 2 * (NT / 32));
 
   const Unit un = p.units[blockIdx.x];
-  const GridDev<T> &gd = reinterpret_cast<const GridDev<T> *>(p.grids)[un.g];
-  SolveState *st = gd.st;
+  const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
+  SolveState *st = gdp->st;
   LaunchState *ls = p.ls;
   const int kind = p.kind;
+  const int tid = threadIdx.x;
 
-  if (p.guard && blockIdx.x == 0 && threadIdx.x == 0) {
+  if (p.guard && blockIdx.x == 0 && tid == 0) {
     // loop exit and runaway guard (count and wall clock) of the loop graph
     const int l = atomicAdd(&ls->launches, 1) + 1;
     const uint64_t now = global_ns();
@@ -231,121 +334,116 @@ __global__ void __launch_bounds__(TX) k_stencil(KParams p) {
   if ((kind == K1_ITER || kind == K1_RESID_INIT) && *(volatile int32_t *)&st->done) return;
   if (kind == K1_RESID_CHECK && *(volatile int32_t *)&st->retired) return;
 
-  const int nx = gd.nx, ny = gd.ny, pitch = gd.pitch;
-  const int i0 = un.sx * TX, j0 = un.sy * gd.ty;
-  const int rend = min(j0 + gd.ty, ny);
+  const int nx = gdp->nx, ny = gdp->ny, pitch = gdp->pitch, ty = gdp->ty;
+  const int i0 = un.sx * TX, j0 = un.sy * ty;
+  const int rend = min(j0 + ty, ny);
   const int mlo = j0 - 1, mhi = rend;          // rows streamed: south halo row .. north look-ahead row
-  const int tid = threadIdx.x;
-  const T beta = (kind == K1_ITER) ? (T)st->beta : (T)0;
-  const T pend = (kind == K1_ITER) ? (T)st->pending : (T)0;
-  const int dsel = st->dsel;
-  const int rsel1 = st->rsel;
-
-  const T *src = (kind == K1_ITER) ? gd.s : (kind == K1_SPMV) ? gd.d[0] : gd.x;
-  const T *dold = gd.d[dsel];
-  const T *xb = (kind == K1_ITER) ? gd.x : gd.b;
-
-  const bool skip_first = (p.dbg_skip_unit == (int)blockIdx.x);
-
-  auto issue = [&](int m) {
-    const int slot = (m - mlo) % G::NST;
-    T *sl = ring + (size_t)slot * G::SLOT;
-    const size_t rowoff = (size_t)m * pitch;
-    uint32_t bytes = G::WS * sizeof(T);
-    const bool need_d = (kind == K1_ITER);
-    const bool need_n = (m < mhi);
-    const bool need_row = (m >= j0 && m < mhi);
-    const bool need_x = need_row && kind != K1_SPMV;
-    if (need_d) bytes += G::WS * sizeof(T);
-    if (need_n) bytes += G::WT * sizeof(T);
-    if (need_row) bytes += (G::WE + G::WT) * sizeof(T);
-    if (need_x) bytes += G::WT * sizeof(T);
-    mbar_arrive_expect_tx(&bar[slot], bytes);
-    if (!(skip_first && m == mlo)) bulk_g2s(sl + G::OFF_S, src + rowoff + i0 - G::H, G::WS * sizeof(T), &bar[slot]);
-    if (need_d) bulk_g2s(sl + G::OFF_D, dold + rowoff + i0 - G::H, G::WS * sizeof(T), &bar[slot]);
-    if (need_n) bulk_g2s(sl + G::OFF_N, gd.cn + rowoff + i0, G::WT * sizeof(T), &bar[slot]);
-    if (need_row) {
-      bulk_g2s(sl + G::OFF_E, gd.ce + rowoff + i0 - G::H, G::WE * sizeof(T), &bar[slot]);
-      bulk_g2s(sl + G::OFF_A, gd.a + rowoff + i0, G::WT * sizeof(T), &bar[slot]);
-    }
-    if (need_x) bulk_g2s(sl + G::OFF_X, xb + rowoff + i0, G::WT * sizeof(T), &bar[slot]);
-  };
+  const int dsel = st->dsel, rsel = st->rsel;
+  const size_t pitch_b = (size_t)pitch * sizeof(T);
+  constexpr int SLOTB = G::SLOT * (int)sizeof(T);
 
   if (tid == 0) {
-    for (int s = 0; s < G::NST; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < G::NST; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    ctl[0] = 0; ctl[1] = mlo - 1; ctl[2] = mlo - 1;
     fence_mbar_init();
   }
   __syncthreads();
-  int issued = min(mhi, mlo + G::NST - 1);   // last row handed to the copy engine (thread 0)
-  if (tid == 0) {
-    for (int m = mlo; m <= issued; ++m) issue(m);
-  }
 
   double acc0 = 0.0, acc1 = 0.0;
-  bool ok = true;
-  int failed_at = mhi + 1;
-  for (int m = mlo; m <= mhi; ++m) {
-    const int slot = (m - mlo) % G::NST;
-    const uint32_t parity = (uint32_t)(((m - mlo) / G::NST) & 1);
-    const bool got = mbar_wait_bounded(&bar[slot], parity, p.timeout_ns);
-    if (!__syncthreads_and(got)) { ok = false; failed_at = m; break; }
-    const T *sl = ring + (size_t)slot * G::SLOT;
-    T *dnm = dn + (size_t)((m + 6) % 3) * G::WDN;
-    // d' on row m over columns [i0-1, i0+TX+1)
-    for (int c = tid; c < G::WDN; c += TX) {
-      const int k = c - 1 + G::H;
-      T v = sl[G::OFF_S + k];
-      if (kind == K1_ITER) v = fma(beta, sl[G::OFF_D + k], v);
-      dnm[c] = v;
+  if (tid >= TX) {
+    // ---- producer warp
+    const int lane = tid - TX;
+    RowCopy c{nullptr, 0, 0, 0};
+    const T *src = (kind == K1_ITER) ? gdp->s : (kind == K1_SPMV) ? gdp->d[0] : gdp->x;
+    auto at = [&](const T *plane, int col) { return reinterpret_cast<const char *>(plane + i0 + col); };
+    switch (lane) {
+      case 0: c = RowCopy{at(src, -G::H), (uint32_t)(G::OFF_S * sizeof(T)), (uint32_t)(G::WS * sizeof(T)), 0}; break;
+      case 1: if (kind == K1_ITER) c = RowCopy{at(gdp->d[dsel], -G::H), (uint32_t)(G::OFF_D * sizeof(T)), (uint32_t)(G::WS * sizeof(T)), 0}; break;
+      case 2: c = RowCopy{at(gdp->cn, 0), (uint32_t)(G::OFF_N * sizeof(T)), (uint32_t)(G::WT * sizeof(T)), 1}; break;
+      case 3: c = RowCopy{at(gdp->ce, -G::H), (uint32_t)(G::OFF_E * sizeof(T)), (uint32_t)(G::WE * sizeof(T)), 2}; break;
+      case 4: c = RowCopy{at(gdp->a, 0), (uint32_t)(G::OFF_A * sizeof(T)), (uint32_t)(G::WT * sizeof(T)), 2}; break;
+      case 5: if (kind != K1_SPMV) c = RowCopy{at(kind == K1_ITER ? gdp->x : gdp->b, 0), (uint32_t)(G::OFF_X * sizeof(T)), (uint32_t)(G::WT * sizeof(T)), 2}; break;
+      default: break;
     }
-    __syncthreads();
-    const int r = m - 1;
-    if (r >= j0) {
-      const int col = i0 + tid;
-      if (col < nx) {
-        const T *slr = ring + (size_t)((r - mlo) % G::NST) * G::SLOT;
-        const T *sls = ring + (size_t)((r - 1 - mlo) % G::NST) * G::SLOT;
-        const T *dr = dn + (size_t)((r + 6) % 3) * G::WDN;
-        const T *ds = dn + (size_t)((r - 1 + 6) % 3) * G::WDN;
-        const T c_ctr = dr[tid + 1];
-        T av = -sls[G::OFF_N + tid] * ds[tid + 1];
-        av = fma(-slr[G::OFF_E + G::H + tid - 1], dr[tid], av);
-        av = fma(slr[G::OFF_A + tid], c_ctr, av);
-        av = fma(-slr[G::OFF_E + G::H + tid], dr[tid + 2], av);
-        av = fma(-slr[G::OFF_N + tid], dnm[tid + 1], av);
-        const size_t ro = (size_t)r * pitch;
-        if (kind == K1_ITER) {
-          const T xv = fma(pend, slr[G::OFF_D + G::H + tid], slr[G::OFF_X + tid]);
-          store_dup(gd.d[dsel ^ 1] + ro, col, nx, c_ctr);
-          store_dup(gd.x + ro, col, nx, xv);
-          store_dup(gd.q + ro, col, nx, av);
-          acc0 = fma((double)c_ctr, (double)av, acc0);
-        } else if (kind == K1_SPMV) {
-          store_dup(gd.q + ro, col, nx, av);
-        } else {
-          const T bv = slr[G::OFF_X + tid];
-          const T rv = bv - av;
-          store_dup(gd.r[rsel1] + ro, col, nx, rv);
-          acc0 = fma((double)rv, (double)rv, acc0);
-          acc1 = fma((double)bv, (double)bv, acc1);
+    const bool skip_first = (p.dbg_skip_unit == (int)blockIdx.x) && lane == 0;
+    const int last = produce_rows<G::NST>(c, ring_b, SLOTB, full, empty, mlo, mhi, pitch_b, j0, skip_first,
+                                          p.timeout_ns, ctl);
+    if (lane == 0) ctl[1] = last;
+  } else {
+    // ---- compute threads
+    const T beta = (kind == K1_ITER) ? (T)st->beta : (T)0;
+    const T pend = (kind == K1_ITER) ? (T)st->pending : (T)0;
+    T *const d_out = gdp->d[dsel ^ 1];
+    T *const x_out = gdp->x;
+    T *const q_out = gdp->q;
+    T *const r_out = gdp->r[rsel];
+    int consumed = mlo - 1;
+    for (int m = mlo; m <= mhi + 1; ++m) {
+      bool got = true;
+      if (m <= mhi) {
+        const int slot = (m - mlo) % G::NST;
+        got = mbar_wait_bounded(&full[slot], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
+        const T *sl = ring + (size_t)slot * G::SLOT;
+        T *dnm = dn + (size_t)((m + 8) % G::NDN) * G::WDN;
+        // d' on row m over columns [i0-1, i0+TX+1)
+        for (int c = tid; c < G::WDN; c += TX) {
+          const int k = c - 1 + G::H;
+          T v = sl[G::OFF_S + k];
+          if (kind == K1_ITER) v = fma(beta, sl[G::OFF_D + k], v);
+          dnm[c] = v;
         }
       }
+      const int r = m - 2;
+      if (r >= j0 && r < rend) {
+        const int col = i0 + tid;
+        if (col < nx) {
+          const T *slr = ring + (size_t)((r - mlo) % G::NST) * G::SLOT;
+          const T *sls = ring + (size_t)((r - 1 - mlo) % G::NST) * G::SLOT;
+          const T *dr = dn + (size_t)((r + 8) % G::NDN) * G::WDN;
+          const T *ds = dn + (size_t)((r - 1 + 8) % G::NDN) * G::WDN;
+          const T *dnn = dn + (size_t)((r + 1 + 8) % G::NDN) * G::WDN;
+          const T c_ctr = dr[tid + 1];
+          T av = -sls[G::OFF_N + tid] * ds[tid + 1];
+          av = fma(-slr[G::OFF_E + G::H + tid - 1], dr[tid], av);
+          av = fma(slr[G::OFF_A + tid], c_ctr, av);
+          av = fma(-slr[G::OFF_E + G::H + tid], dr[tid + 2], av);
+          av = fma(-slr[G::OFF_N + tid], dnn[tid + 1], av);
+          const size_t ro = (size_t)r * pitch;
+          if (kind == K1_ITER) {
+            const T xv = fma(pend, slr[G::OFF_D + G::H + tid], slr[G::OFF_X + tid]);
+            store_dup(d_out + ro, col, nx, c_ctr);
+            store_dup(x_out + ro, col, nx, xv);
+            store_dup(q_out + ro, col, nx, av);
+            acc0 = fma(to_f64(c_ctr), to_f64(av), acc0);
+          } else if (kind == K1_SPMV) {
+            store_dup(q_out + ro, col, nx, av);
+          } else {
+            const T bv = slr[G::OFF_X + tid];
+            const T rv = bv - av;
+            store_dup(r_out + ro, col, nx, rv);
+            acc0 = fma(to_f64(rv), to_f64(rv), acc0);
+            acc1 = fma(to_f64(bv), to_f64(bv), acc1);
+          }
+        }
+      }
+      if (!compute_sync_and<TX>(got)) {
+        if (tid == 0) { ctl[0] = 1; flag_timeout(st); }
+        break;
+      }
+      if (m <= mhi) consumed = m;
+      // row m-3 is finished: its slot may be refilled
+      if (tid == 0 && m - 3 >= mlo && m - 3 + G::NST <= mhi) mbar_arrive(&empty[(m - 3 - mlo) % G::NST]);
     }
-    __syncthreads();
-    // the slot of row m-2 is free: refill it with row m-2+NST
-    if (tid == 0 && m - 2 >= mlo) {
-      const int nm = m - 2 + G::NST;
-      if (nm <= mhi) { fence_proxy_async(); issue(nm); issued = nm; }
-    }
+    if (tid == 0) ctl[2] = consumed;
   }
-  if (!ok && tid == 0) {
-    // give up: record it, and wait (bounded) for the copies still in flight
-    flag_timeout(st);
-    for (int m = failed_at; m <= issued; ++m)
-      mbar_wait_bounded(&bar[(m - mlo) % G::NST], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
+  __syncthreads();
+  if (tid == 0 && ctl[2] < ctl[1]) {
+    // the compute threads gave up: wait (bounded) for the rows still in flight
+    for (int m = ctl[2] + 1; m <= ctl[1]; ++m)
+      mbar_wait_bounded(&full[(m - mlo) % G::NST], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
   }
   if (kind == K1_SPMV) return;
-  if (grid_reduce2<TX>(acc0, acc1, gd.partial, un.u, gd.n_units, &st->cnt1, red, flag)) {
+  if (grid_reduce2<NT>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt1, red, flag)) {
     if (threadIdx.x == 0) {
       if (kind == K1_ITER) {
         const double dq = acc0;
@@ -369,9 +467,12 @@ __global__ void __launch_bounds__(TX) k_stencil(KParams p) {
 }
 
 // ------------------------------------------------------------ kernel 2
-// Preconditioner pass (Algorithm 1, line 7): r' = r - alpha q;
-// s = Z (D^-1 (Z^T r')); sums s.r' and r'.r'. Kinds: K2_ITER, K2_INIT
-// (alpha = 0, q not read), K2_APPLY (s = M^-1 r only, r in r[0]).
+// Preconditioner pass (the residual update and preconditioning step of
+// Algorithm 1): r' = r - alpha q; s = Z (D^-1 (Z^T r')); sums s.r' and r'.r'.
+// Kinds: K2_ITER, K2_INIT (alpha = 0, q not read), K2_APPLY (s = M^-1 r only,
+// r in r[0]). Step m computes r' on row m, t = D^-1 Z^T r' on row m - 1 (Z^T
+// pulls from rows m-1-LD..m-1, finished before) and s = Z t on row m - 2 - LD
+// (Z pushes from rows up to m - 2): one compute barrier per row.
 template <typename T, int TX, class P>
 struct K2Geom {
   static constexpr int AL = 16 / (int)sizeof(T);
@@ -381,162 +482,172 @@ struct K2Geom {
   static constexpr int WR = TX + 2 * HR, WZ = TX + 2 * HZ;
   static constexpr int WRC = TX + 4 * R;             // r' computed on [i0-2R, i0+TX+2R)
   static constexpr int WTC = TX + 2 * R;             // t computed on [i0-R, i0+TX+R)
-  static constexpr int RING = LD + 1;                // rows of r' and of t kept
-  static constexpr int NST = LD + 1 + 3;             // ring slots
+  static constexpr int NRN = LD + 3;                 // rows of r' kept (m-2-LD .. m)
+  static constexpr int NTT = LD + 2;                 // rows of t kept (m-2-LD .. m-1)
+  // rows streamed ahead: binary64 is bound by the FP64 pipe, so shared memory
+  // goes to CTAs (latency hiding for the FP64 work); binary32 is bound by
+  // HBM, so it goes to rows in flight
+  static constexpr int PF = sizeof(T) == 8 ? 1 : 2;
+  static constexpr int NST = LD + 3 + PF;            // ring slots: rows m-2-LD .. m live
+  static constexpr int NT = TX + 32;                 // compute threads + producer warp
   static constexpr int OFF_R = 0, OFF_Q = WR, OFF_Z = 2 * WR, OFF_DI = 2 * WR + NZ * WZ, SLOT = OFF_DI + WZ;
   static constexpr size_t SMEM =
-      128 + sizeof(T) * ((size_t)NST * SLOT + (size_t)RING * WRC + (size_t)RING * WTC) + 16 * 2 * (TX / 32) + 64;
+      256 + sizeof(T) * ((size_t)NST * SLOT + (size_t)NRN * WRC + (size_t)NTT * WTC) + 16 * (NT / 32) + 64;
 };
 
 template <typename T, int TX, class P>
-__global__ void __launch_bounds__(TX) k_precond(KParams p) {
+__global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
   using G = K2Geom<T, TX, P>;
-  constexpr int R = P::R, LD = P::LD, NZ = P::NZ, NW = P::NW;
+  constexpr int R = P::R, LD = P::LD, NZ = P::NZ, NW = P::NW, NT = G::NT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
-  T *ring = reinterpret_cast<T *>(smem_raw + 128);
-  T *rn = ring + (size_t)G::NST * G::SLOT;
-  T *tt = rn + (size_t)G::RING * G::WRC;
-  double *red = reinterpret_cast<double *>(tt + (size_t)G::RING * G::WTC);
-  int *flag = reinterpret_cast<int *>(red + 2 * (TX / 32));
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
+  uint64_t *empty = full + G::NST;
+  volatile int *ctl = reinterpret_cast<volatile int *>(smem_raw + 224);
+  unsigned char *ring_b = smem_raw + 256;
+  const T *ring = reinterpret_cast<const T *>(ring_b);
+  T *rn = reinterpret_cast<T *>(ring_b + sizeof(T) * (size_t)G::NST * G::SLOT);
+  T *tt = rn + (size_t)G::NRN * G::WRC;
+  double *red = reinterpret_cast<double *>(tt + (size_t)G::NTT * G::WTC);
+  int *flag = reinterpret_cast<int *>(red + 2 * (NT / 32));
 
   const Unit un = p.units[blockIdx.x];
-  const GridDev<T> &gd = reinterpret_cast<const GridDev<T> *>(p.grids)[un.g];
-  SolveState *st = gd.st;
+  const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
+  SolveState *st = gdp->st;
   LaunchState *ls = p.ls;
   const int kind = p.kind;
+  const int tid = threadIdx.x;
 
   if (kind == K2_ITER && p.use_cond && *(volatile int32_t *)&ls->stop) return;
   if (kind != K2_APPLY && *(volatile int32_t *)&st->done) return;
 
-  const int nx = gd.nx, ny = gd.ny, pitch = gd.pitch;
-  const int i0 = un.sx * TX, j0 = un.sy * gd.ty;
-  const int rend = min(j0 + gd.ty, ny);
+  const int nx = gdp->nx, ny = gdp->ny, pitch = gdp->pitch, ty = gdp->ty;
+  const int i0 = un.sx * TX, j0 = un.sy * ty;
+  const int rend = min(j0 + ty, ny);
   const int mlo = j0 - LD, mhi = rend + LD - 1;
-  const int tid = threadIdx.x;
-  const T alpha = (kind == K2_ITER) ? (T)st->alpha : (T)0;
   const int rsel = (kind == K2_APPLY) ? 0 : st->rsel;
-  const T *rin = gd.r[rsel];
-  T *rout = gd.r[rsel ^ 1];
-  const bool skip_first = (p.dbg_skip_unit == (int)blockIdx.x);
-
-  auto issue = [&](int m) {
-    const int slot = (m - mlo) % G::NST;
-    T *sl = ring + (size_t)slot * G::SLOT;
-    const size_t rowoff = (size_t)m * pitch;
-    const bool need_q = (kind == K2_ITER);
-    const bool need_z = (m >= j0);
-    uint32_t bytes = G::WR * sizeof(T);
-    if (need_q) bytes += G::WR * sizeof(T);
-    if (need_z) bytes += (NZ + 1) * G::WZ * sizeof(T);
-    mbar_arrive_expect_tx(&bar[slot], bytes);
-    if (!(skip_first && m == mlo)) bulk_g2s(sl + G::OFF_R, rin + rowoff + i0 - G::HR, G::WR * sizeof(T), &bar[slot]);
-    if (need_q) bulk_g2s(sl + G::OFF_Q, gd.q + rowoff + i0 - G::HR, G::WR * sizeof(T), &bar[slot]);
-    if (need_z) {
-#pragma unroll
-      for (int s = 0; s < NZ; ++s)
-        bulk_g2s(sl + G::OFF_Z + s * G::WZ, gd.z[s] + rowoff + i0 - G::HZ, G::WZ * sizeof(T), &bar[slot]);
-      bulk_g2s(sl + G::OFF_DI, gd.dinv + rowoff + i0 - G::HZ, G::WZ * sizeof(T), &bar[slot]);
-    }
-  };
+  const size_t pitch_b = (size_t)pitch * sizeof(T);
+  constexpr int SLOTB = G::SLOT * (int)sizeof(T);
 
   if (tid == 0) {
-    for (int s = 0; s < G::NST; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < G::NST; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    ctl[0] = 0; ctl[1] = mlo - 1; ctl[2] = mlo - 1;
     fence_mbar_init();
   }
   __syncthreads();
-  int issued = min(mhi, mlo + G::NST - 1);
-  if (tid == 0) {
-    for (int m = mlo; m <= issued; ++m) issue(m);
-  }
 
   double acc0 = 0.0, acc1 = 0.0;
-  bool ok = true;
-  int failed_at = mhi + 1;
-  for (int m = mlo; m <= mhi; ++m) {
-    const int slot = (m - mlo) % G::NST;
-    const uint32_t parity = (uint32_t)(((m - mlo) / G::NST) & 1);
-    const bool got = mbar_wait_bounded(&bar[slot], parity, p.timeout_ns);
-    if (!__syncthreads_and(got)) { ok = false; failed_at = m; break; }
-    const T *sl = ring + (size_t)slot * G::SLOT;
-    // r' on row m over [i0-2R, i0+TX+2R)
-    T *rnm = rn + (size_t)((m + 8) % G::RING) * G::WRC;
-    for (int c = tid; c < G::WRC; c += TX) {
-      const int k = c + G::HR - 2 * R;
-      T v = sl[G::OFF_R + k];
-      if (kind == K2_ITER) v = fma(-alpha, sl[G::OFF_Q + k], v);
-      rnm[c] = v;
-    }
-    __syncthreads();
-    // t = D^-1 (Z^T r') on row m over [i0-R, i0+TX+R)
-    if (m >= j0) {
-      T *tm = tt + (size_t)((m + 8) % G::RING) * G::WTC;
-      for (int c = tid; c < G::WTC; c += TX) {
-        T acc = (T)0;
-        if (m < ny) {
-          const int kz = c + G::HZ - R;
-          acc = rnm[c + R];
+  if (tid >= TX) {
+    // ---- producer warp
+    const int lane = tid - TX;
+    auto at = [&](const T *plane, int col) { return reinterpret_cast<const char *>(plane + i0 + col); };
+    RowCopy c{nullptr, 0, 0, 0};
+    if (lane == 0) c = RowCopy{at(gdp->r[rsel], -G::HR), (uint32_t)(G::OFF_R * sizeof(T)), (uint32_t)(G::WR * sizeof(T)), 0};
+    else if (lane == 1) { if (kind == K2_ITER) c = RowCopy{at(gdp->q, -G::HR), (uint32_t)(G::OFF_Q * sizeof(T)), (uint32_t)(G::WR * sizeof(T)), 0}; }
+    else if (lane - 2 < NZ) c = RowCopy{at(gdp->z[lane - 2], -G::HZ), (uint32_t)((G::OFF_Z + (lane - 2) * G::WZ) * sizeof(T)), (uint32_t)(G::WZ * sizeof(T)), 3};
+    else if (lane - 2 == NZ) c = RowCopy{at(gdp->dinv, -G::HZ), (uint32_t)(G::OFF_DI * sizeof(T)), (uint32_t)(G::WZ * sizeof(T)), 3};
+    const bool skip_first = (p.dbg_skip_unit == (int)blockIdx.x) && lane == 0;
+    const int last = produce_rows<G::NST>(c, ring_b, SLOTB, full, empty, mlo, mhi, pitch_b, j0, skip_first,
+                                          p.timeout_ns, ctl);
+    if (lane == 0) ctl[1] = last;
+  } else {
+    // ---- compute threads
+    const T alpha = (kind == K2_ITER) ? (T)st->alpha : (T)0;
+    T *const rout = gdp->r[rsel ^ 1];
+    T *const s_out = gdp->s;
+    const T *const zwrap = gdp->zwrap;
+    // the strips holding the first or last columns apply the periodic side table
+    const bool edge = NW > 0 && (i0 < 2 * R + 2 || i0 + TX + 2 * R + 2 > nx);
+    int consumed = mlo - 1;
+    for (int m = mlo; m <= rend + LD + 1; ++m) {
+      bool got = true;
+      // r' on row m over [i0-2R, i0+TX+2R)
+      if (m <= mhi) {
+        const int slot = (m - mlo) % G::NST;
+        got = mbar_wait_bounded(&full[slot], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
+        const T *sl = ring + (size_t)slot * G::SLOT;
+        T *rnm = rn + (size_t)((m + 8) % G::NRN) * G::WRC;
+        for (int c = tid; c < G::WRC; c += TX) {
+          const int k = c + G::HR - 2 * R;
+          T v = sl[G::OFF_R + k];
+          if (kind == K2_ITER) v = fma(-alpha, sl[G::OFF_Q + k], v);
+          rnm[c] = v;
+        }
+      }
+      // t = D^-1 (Z^T r') on row mt = m - 1 over [i0-R, i0+TX+R)
+      const int mt = m - 1;
+      if (mt >= j0 && mt <= mhi) {
+        const T *sl = ring + (size_t)((mt - mlo) % G::NST) * G::SLOT;
+        const T *rnt = rn + (size_t)((mt + 8) % G::NRN) * G::WRC;
+        T *tm = tt + (size_t)((mt + 8) % G::NTT) * G::WTC;
+        for (int c = tid; c < G::WTC; c += TX) {
+          T acc = (T)0;
+          if (mt < ny) {
+            const int kz = c + G::HZ - R;
+            acc = rnt[c + R];
+#pragma unroll
+            for (int s = 0; s < NZ; ++s) {
+              const T *rrow = rn + (size_t)((mt + P::dy(s) + 8) % G::NRN) * G::WRC;
+              acc = fma(sl[G::OFF_Z + s * G::WZ + kz], rrow[c + R + P::dx(s)], acc);
+            }
+            if (edge) {
+              const int col = i0 - R + c;
+              const int cm = col < 0 ? col + nx : (col >= nx ? col - nx : col);
+#pragma unroll
+              for (int w = 0; w < (NW > 0 ? NW : 1); ++w)
+                if (cm == nx - 1 - P::wcol(w)) acc = fma(zwrap[(size_t)mt * NW + w], rnt[c + R + P::wdx(w)], acc);
+            }
+            acc *= sl[G::OFF_DI + kz];
+          }
+          tm[c] = acc;
+        }
+      }
+      // s = Z t on row r = m - 2 - LD
+      const int r = m - 2 - LD;
+      if (r >= j0 && r < rend) {
+        const int col = i0 + tid;
+        if (col < nx) {
+          const T *tr = tt + (size_t)((r + 8) % G::NTT) * G::WTC;
+          T acc = tr[tid + R];
 #pragma unroll
           for (int s = 0; s < NZ; ++s) {
-            const T *rrow = rn + (size_t)((m + P::dy(s) + 8) % G::RING) * G::WRC;
-            acc = fma(sl[G::OFF_Z + s * G::WZ + kz], rrow[c + R + P::dx(s)], acc);
+            const int rowz = r - P::dy(s);           // row of the column holding Z[(col,r), that column]
+            const T *slz = ring + (size_t)((rowz - mlo) % G::NST) * G::SLOT;
+            const T *trow = tt + (size_t)((rowz + 8) % G::NTT) * G::WTC;
+            acc = fma(slz[G::OFF_Z + s * G::WZ + tid - P::dx(s) + G::HZ], trow[tid + R - P::dx(s)], acc);
           }
-          if (NW > 0) {
-            const int col = i0 - R + c;
-            const int cm = ((col % nx) + nx) % nx;
+          if (edge) {
 #pragma unroll
-            for (int w = 0; w < (NW > 0 ? NW : 1); ++w)
-              if (cm == nx - 1 - P::wcol(w)) acc = fma(gd.zwrap[(size_t)m * NW + w], rnm[c + R + P::wdx(w)], acc);
+            for (int w = 0; w < (NW > 0 ? NW : 1); ++w) {
+              const int target = P::wdx(w) - 1 - P::wcol(w);   // 0 or 1
+              if (col == target) acc = fma(zwrap[(size_t)r * NW + w], tr[tid + R - P::wdx(w)], acc);
+            }
           }
-          acc *= sl[G::OFF_DI + kz];
+          const T *rnr = rn + (size_t)((r + 8) % G::NRN) * G::WRC;
+          const T rv = rnr[tid + 2 * R];
+          const size_t ro = (size_t)r * pitch;
+          store_dup(s_out + ro, col, nx, acc);
+          if (kind != K2_APPLY) store_dup(rout + ro, col, nx, rv);
+          acc0 = fma(to_f64(acc), to_f64(rv), acc0);
+          acc1 = fma(to_f64(rv), to_f64(rv), acc1);
         }
-        tm[c] = acc;
       }
-    }
-    __syncthreads();
-    // s = Z t on row r = m - LD
-    const int r = m - LD;
-    if (r >= j0) {
-      const int col = i0 + tid;
-      if (col < nx) {
-        const T *tr = tt + (size_t)((r + 8) % G::RING) * G::WTC;
-        T acc = tr[tid + R];
-#pragma unroll
-        for (int s = 0; s < NZ; ++s) {
-          const int rowz = r - P::dy(s);           // row of the column holding Z[(col,r), that column]
-          const T *slz = ring + (size_t)((rowz - mlo) % G::NST) * G::SLOT;
-          const T *trow = tt + (size_t)((rowz + 8) % G::RING) * G::WTC;
-          acc = fma(slz[G::OFF_Z + s * G::WZ + tid - P::dx(s) + G::HZ], trow[tid + R - P::dx(s)], acc);
-        }
-        if (NW > 0) {
-#pragma unroll
-          for (int w = 0; w < (NW > 0 ? NW : 1); ++w) {
-            const int target = ((P::wdx(w) - 1 - P::wcol(w)) % nx + nx) % nx;
-            if (col == target) acc = fma(gd.zwrap[(size_t)r * NW + w], tr[tid + R - P::wdx(w)], acc);
-          }
-        }
-        const T *rnr = rn + (size_t)((r + 8) % G::RING) * G::WRC;
-        const T rv = rnr[tid + 2 * R];
-        const size_t ro = (size_t)r * pitch;
-        store_dup(gd.s + ro, col, nx, acc);
-        if (kind != K2_APPLY) store_dup(rout + ro, col, nx, rv);
-        acc0 = fma((double)acc, (double)rv, acc0);
-        acc1 = fma((double)rv, (double)rv, acc1);
+      if (!compute_sync_and<TX>(got)) {
+        if (tid == 0) { ctl[0] = 1; flag_timeout(st); }
+        break;
       }
+      if (m <= mhi) consumed = m;
+      // row m-2-LD is finished: its slot may be refilled
+      if (tid == 0 && m - 2 - LD >= mlo && m - 2 - LD + G::NST <= mhi) mbar_arrive(&empty[(m - 2 - LD - mlo) % G::NST]);
     }
-    __syncthreads();
-    if (tid == 0 && m - LD >= mlo) {
-      const int nm = m - LD + G::NST;
-      if (nm <= mhi) { fence_proxy_async(); issue(nm); issued = nm; }
-    }
+    if (tid == 0) ctl[2] = consumed;
   }
-  if (!ok && tid == 0) {
-    flag_timeout(st);
-    for (int m = failed_at; m <= issued; ++m)
-      mbar_wait_bounded(&bar[(m - mlo) % G::NST], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
+  __syncthreads();
+  if (tid == 0 && ctl[2] < ctl[1]) {
+    for (int m = ctl[2] + 1; m <= ctl[1]; ++m)
+      mbar_wait_bounded(&full[(m - mlo) % G::NST], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
   }
   if (kind == K2_APPLY) return;
-  if (grid_reduce2<TX>(acc0, acc1, gd.partial, un.u, gd.n_units, &st->cnt2, red, flag)) {
+  if (grid_reduce2<NT>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt2, red, flag)) {
     if (threadIdx.x == 0) {
       const double rho_new = acc0, rr = acc1;
       st->rr = rr;
@@ -597,6 +708,44 @@ __global__ void __launch_bounds__(TX) k_pack(KParams p, const U *user, int which
       store_dup(dst + ro, col, gd.nx, v);
     }
   }
+}
+
+// Mixed precision, refinement step: the binary64 residual r (plane r[rsel] of
+// the binary64 grid) scaled by a power of two becomes the binary32 right-hand
+// side b of the inner solve.
+template <int TX>
+__global__ void __launch_bounds__(TX) k_residual_to_f32(const GridDev<double> *g64, const GridDev<float> *g32,
+                                                     const Unit *units, double scale) {
+  const Unit un = units[blockIdx.x];
+  const GridDev<double> &a = g64[un.g];
+  const GridDev<float> &f = g32[un.g];
+  if (*(volatile int32_t *)&a.st->retired) return;
+  const int col = un.sx * TX + threadIdx.x;
+  const int j0 = un.sy * a.ty, rend = min(j0 + a.ty, a.ny);
+  const double *r = a.r[a.st->rsel];
+  const double sc = scale;
+  float *b = const_cast<float *>(f.b);
+  if (col < a.nx)
+    for (int j = j0; j < rend; ++j)
+      store_dup(b + (size_t)j * f.pitch, col, a.nx, (float)(r[(size_t)j * a.pitch + col] * sc));
+}
+
+// Mixed precision, refinement step: x += e / scale with e the binary32 inner
+// solution (x plane of the binary32 grid); the update is done in binary64.
+template <int TX>
+__global__ void __launch_bounds__(TX) k_correct_f64(const GridDev<double> *g64, const GridDev<float> *g32,
+                                                  const Unit *units, double inv_scale) {
+  const Unit un = units[blockIdx.x];
+  const GridDev<double> &a = g64[un.g];
+  const GridDev<float> &f = g32[un.g];
+  if (*(volatile int32_t *)&a.st->retired) return;
+  const int col = un.sx * TX + threadIdx.x;
+  const int j0 = un.sy * a.ty, rend = min(j0 + a.ty, a.ny);
+  if (col < a.nx)
+    for (int j = j0; j < rend; ++j) {
+      double *xr = a.x + (size_t)j * a.pitch;
+      store_dup(xr, col, a.nx, fma(to_f64(f.x[(size_t)j * f.pitch + col]), inv_scale, xr[col]));
+    }
 }
 
 // padded plane -> user [ny][nx] (land = 0), over every cell

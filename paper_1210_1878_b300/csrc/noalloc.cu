@@ -96,7 +96,7 @@ extern "C" int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void 
     void *pack_args[] = {&p, (void *)&vin, &which};
     CK(cudaLaunchKernel(P.ks.pack, dim3(P.n_units), dim3(P.tx), pack_args, 0, s));
     void *k_args[] = {&p};
-    CK(cudaLaunchKernel(P.ks.k1, dim3(P.n_units), dim3(P.tx), k_args, P.ks.smem1, s));
+    CK(cudaLaunchKernel(P.ks.k1, dim3(P.n_units), dim3(P.ks.tb), k_args, P.ks.smem1, s));
   }
   const GridDev<double> *gdp = reinterpret_cast<const GridDev<double> *>(b8);
   double *qout = q;

@@ -2,7 +2,7 @@
 
 Element by element on seeded grids that span several strips and a ragged
 last strip; tolerances follow from binary64 rounding of the stated
-operations (Section 3, Eq. 9 for A; Algorithm 1 line 7 for M^-1 = Z D^-1 Z^T;
+operations (Section 3, Eq. 9 for A; the preconditioning step of Algorithm 1 for M^-1 = Z D^-1 Z^T;
 Algorithm 1 for the solve, whose result is judged by the residual and by the
 distance to a tight reference solution)."""
 import numpy as np
