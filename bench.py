@@ -47,7 +47,14 @@ WORKLOADS = {
     "orca12-mixed": dict(grid=gridgen.ORCA12, ci=4, pattern=TRIL_A2, tau=0.05, q=0, prec=1, rtol=1e-10),
     "orca12-mixed-trilA": dict(grid=gridgen.ORCA12, ci=4, pattern=TRIL_A, tau=0.0, q=0, prec=1, rtol=1e-10),
     "orca025-mixed": dict(grid=gridgen.ORCA025, ci=2, pattern=TRIL_A2, tau=0.05, q=0, prec=1, rtol=1e-10),
+    # 64 ensemble members of uneven sizes (182x149 .. 1442x1021), one batched call per step
+    "batch64-mixed": dict(kind="batch", ci=3, pattern=TRIL_A2, tau=0.05, q=0, prec=1, rtol=1e-10, members=64),
+    "batch64-fp64": dict(kind="batch", ci=3, pattern=TRIL_A2, tau=0.05, q=0, prec=0, rtol=1e-10, members=64),
+    # open-loop Poisson stream (200 req/s) over resident grids, continuous batching
+    "serve-mixed": dict(kind="serve", ci=4, pattern=TRIL_A2, tau=0.05, q=0, prec=1, rtol=1e-10, rate=200.0,
+                        seconds=60.0, warm_s=5.0),
 }
+BATCH_SIZES = [gridgen.COARSE, gridgen.ORCA1, gridgen.ORCA05, gridgen.ORCA025]
 DEFAULT_WORKLOAD = "orca12-fp64"
 
 # FP64 arithmetic of this B300: 2 FMA per clock per SM (measured 1.87-1.96 at
@@ -206,6 +213,193 @@ def _traffic_record(kernel_key):
     return None
 
 
+def _batch_grids(wl):
+    rng = np.random.default_rng(gridgen.seed_for(wl["ci"]))
+    picks = rng.integers(0, len(BATCH_SIZES), size=wl["members"])
+    return [gridgen.make_grid(seed=gridgen.seed_for(wl["ci"], m), **BATCH_SIZES[k]) for m, k in enumerate(picks)]
+
+
+def _sample_clocks(gpu):
+    c = ClockSampler(gpu)
+    c.start()
+    time.sleep(0.3)
+    return c
+
+
+def run_batch(args, wl_name, wl):
+    """64 uneven ensemble grids solved together per step (one pcg_solve_batched
+    call: every launch covers the work units of all unconverged members, the
+    loop runs in a conditional CUDA graph). Also times the same 64 as
+    sequential binary64 single solves."""
+    import torch
+    import paper_1210_1878_b300 as pcg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    grids = _batch_grids(wl)
+    t = time.perf_counter()
+    hs = [pcg.ainv_setup_grid(g, pattern=wl["pattern"], drop_tol=wl["tau"], tile_x=args.tile_x, tile_y=args.tile_y)
+          for g in grids]
+    setup_s = time.perf_counter() - t
+    bs = [torch.from_numpy(g.b).cuda() for g in grids]
+    xs = [torch.zeros_like(b) for b in bs]
+    opts = pcg.make_opts(rtol=wl["rtol"], max_iter=5000, prec=wl["prec"], inner_rtol=args.inner_rtol)
+    for _ in range(args.warmup):
+        rc, stats = pcg.pcg_solve_batched(hs, bs, xs, opts)
+    sampler = _sample_clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    l0 = pcg.pcg_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    worst = 0.0
+    for _ in range(args.steps):
+        rc, stats = pcg.pcg_solve_batched(hs, bs, xs, opts)
+        worst = max(worst, max(st.true_relres for st in stats))
+    e1.record()
+    torch.cuda.synchronize()
+    launches = pcg.pcg_kernel_launches() - l0
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    value = len(hs) / (ms / 1e3)
+    # the same members one by one in binary64
+    o64 = pcg.make_opts(rtol=wl["rtol"], max_iter=5000, prec=0)
+    for h, b, x in zip(hs, bs, xs):
+        pcg.pcg_solve(h, b, x, o64)
+    torch.cuda.synchronize()
+    e0.record()
+    for h, b, x in zip(hs, bs, xs):
+        pcg.pcg_solve(h, b, x, o64)
+    e1.record()
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    # end to end with pinned host buffers
+    bh = [torch.from_numpy(g.b.copy()).pin_memory() for g in grids]
+    xh = [torch.zeros_like(b).pin_memory() for b in bh]
+    pcg.pcg_solve_batched(hs, bh, xh, opts)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(max(1, args.e2e_steps)):
+        pcg.pcg_solve_batched(hs, bh, xh, opts)
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / max(1, args.e2e_steps)
+    vec_bytes = sum(g.nx * g.ny * 8 for g in grids)
+    sizes = {}
+    for g in grids:
+        sizes[f"{g.nx}x{g.ny}"] = sizes.get(f"{g.nx}x{g.ny}", 0) + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if wl["prec"] == 1 else "f64", "data": "synthetic",
+        "config": {"workload": wl_name, "members": len(hs), "sizes": sizes,
+                   "pattern": "tril(A^2)", "drop_tol": wl["tau"], "rtol": wl["rtol"],
+                   "worst_true_relres": worst, "setup_s": setup_s,
+                   "sequential_fp64_solves_per_s": len(hs) / (seq_ms / 1e3),
+                   "l2": "members total ~%.2f GB of planes" % (sum(h.resident_bytes for h in hs) / 1e9)},
+        "e2e": {"value": len(hs) / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": vec_bytes,
+                "d2h_bytes_per_step": vec_bytes},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_serve(args, wl_name, wl):
+    """Open-loop Poisson arrivals (mean rate wl['rate']) of solve requests over a
+    resident pool of grids (8 x 362x292, 4 x 1442x1021, 2 x 4322x3059; requests
+    pick a size 60/30/10 and a grid of that size uniformly); each request is
+    the next timestep of its grid (b <- b + 0.01 N(0,1), warm start from the
+    last solution). Latency = submission -> completion."""
+    import torch
+    import paper_1210_1878_b300 as pcg
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rng = np.random.default_rng(gridgen.seed_for(wl["ci"]))
+    pool = [(gridgen.ORCA1, 8), (gridgen.ORCA025, 4), (gridgen.ORCA12, 2)]
+    if args.serve_small:
+        pool = [(gridgen.ORCA1, 8), (gridgen.ORCA025, 4)]
+    grids, size_of = [], []
+    for si, (cfg, cnt) in enumerate(pool):
+        for m in range(cnt):
+            grids.append(gridgen.make_grid(seed=gridgen.seed_for(wl["ci"], 10 * si + m), **cfg))
+            size_of.append(si)
+    hs = [pcg.ainv_setup_grid(g, pattern=wl["pattern"], drop_tol=wl["tau"]) for g in grids]
+    opts = pcg.make_opts(rtol=wl["rtol"], max_iter=5000, prec=wl["prec"], inner_rtol=args.inner_rtol)
+    srv = pcg.Server(hbm_budget_bytes=150 << 30, max_slots=16, chunk_iters=args.chunk, opts=opts)
+    gids = [srv.register(h) for h in hs]
+    # timestep increments (two per grid, reused cyclically, land already zero),
+    # right-hand sides and outputs all on the device
+    cur, noise, outs = [], [], []
+    for k, g in enumerate(grids):
+        wet = torch.from_numpy(g.wet.astype(np.float64)).cuda()
+        cur.append(torch.from_numpy(g.b).cuda())
+        noise.append([wet * torch.from_numpy(0.01 * np.random.default_rng(1000 * k + j).standard_normal((g.ny, g.nx))).cuda()
+                      for j in range(2)])
+        outs.append(torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    seconds = args.serve_seconds if args.serve_seconds > 0 else wl["seconds"]
+    warm_s = min(wl["warm_s"], seconds / 4)
+    total = seconds + warm_s
+    gaps = rng.exponential(1.0 / wl["rate"], size=int(wl["rate"] * total * 1.5) + 10)
+    arrivals = np.cumsum(gaps)
+    arrivals = arrivals[arrivals < total]
+    size_pick = rng.choice(3 if not args.serve_small else 2, size=len(arrivals),
+                           p=[0.6, 0.3, 0.1] if not args.serve_small else [2 / 3, 1 / 3])
+    by_size = {si: [k for k, s_ in enumerate(size_of) if s_ == si] for si in set(size_of)}
+    grid_pick = [by_size[sp][rng.integers(0, len(by_size[sp]))] for sp in size_pick]
+    steps_done = [0] * len(grids)
+    ids = []
+    late = []
+    sampler = _sample_clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    t0 = time.perf_counter()
+    for t_arr, k in zip(arrivals, grid_pick):
+        now = time.perf_counter() - t0
+        if t_arr > now:
+            time.sleep(t_arr - now)
+        else:
+            late.append(now - t_arr)
+        cur[k].add_(noise[k][steps_done[k] % 2])
+        steps_done[k] += 1
+        rid = srv.submit(gids[k], cur[k], outs[k], warm_start=True)
+        ids.append((t_arr, k, rid, time.perf_counter() - t0))
+    results = []
+    for t_arr, k, rid, t_sub in ids:
+        rc, st = srv.wait(rid, timeout_ms=600000)
+        # latency from the scheduled arrival (so a late submission counts against it)
+        results.append((t_arr, k, rc, st.seconds + (t_sub - t_arr), st.true_relres, st.iters))
+    elapsed = time.perf_counter() - t0
+    clocks = sampler.stop()
+    srv_stats = srv.stats()
+    srv.close()
+    meas = [r for r in results if r[0] >= warm_s]
+    lat = np.array([r[3] * 1e3 for r in meas])
+    ok = [r for r in meas if r[2] == pcg.PCG_OK]
+    def pct(a, q):
+        if len(a) == 0:
+            return None
+        srt = np.sort(a)
+        return float(srt[min(len(srt) - 1, max(0, int(math.ceil(q * len(srt))) - 1))])
+    per_size = {}
+    for si in sorted(set(size_of)):
+        ls_ = np.array([r[3] * 1e3 for r in meas if size_of[r[1]] == si])
+        cfg = pool[si][0]
+        per_size[f"{cfg['nx']}x{cfg['ny']}"] = {"n": int(len(ls_)), "p50_ms": pct(ls_, 0.5), "p99_ms": pct(ls_, 0.99)}
+    value = len(results) / elapsed
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": len(results), "warmup": 0,
+        "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if wl["prec"] == 1 else "f64", "data": "synthetic",
+        "config": {"workload": wl_name, "arrival_rate_per_s": wl["rate"], "seconds": seconds, "warm_s": warm_s,
+                   "submit_late_p99_ms": (float(np.percentile(late, 99)) * 1e3) if late else 0.0,
+                   "requests": len(results), "failed": len(results) - sum(1 for r in results if r[2] == 0),
+                   "grids": {f"{c['nx']}x{c['ny']}": n for c, n in pool}, "hbm_budget_gb": 150,
+                   "max_slots": 16, "chunk_iters": args.chunk,
+                   "worst_true_relres": max((r[4] for r in ok), default=None)},
+        "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "mean": float(lat.mean()) if len(lat) else None,
+                       "per_size": per_size},
+        "server_stats": srv_stats, "clocks": clocks,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -219,11 +413,18 @@ def main():
     ap.add_argument("--inner-rtol", type=float, default=0.0)
     ap.add_argument("--tile-x", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0)
+    ap.add_argument("--chunk", type=int, default=8)
+    ap.add_argument("--serve-seconds", type=float, default=0.0)
+    ap.add_argument("--serve-small", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args, args.workload, wl)
+    if wl.get("kind") == "batch":
+        return run_batch(args, args.workload, wl)
+    if wl.get("kind") == "serve":
+        return run_serve(args, args.workload, wl)
 
     import torch
     import paper_1210_1878_b300 as pcg

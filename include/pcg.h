@@ -230,7 +230,7 @@ const char *pcg_last_error_message(void);
 /* ---------------------------------------------------------------- serving */
 
 typedef struct {
-  size_t hbm_budget_bytes;   /* admission limit on the device bytes of registered grids + in-flight work */
+  size_t hbm_budget_bytes;   /* admission limit on the device bytes of registered grids + right-hand-side buffers */
   int32_t max_slots;         /* requests that may be on the device at once (1..256) */
   int32_t chunk_iters;       /* iterations run between admission/retirement points */
   pcg_opts solve;            /* options applied to every request */
@@ -260,10 +260,12 @@ int solver_server_create(const pcg_server_opts *opts, pcg_server **out);
 int solver_server_register(pcg_server *s, pcg_handle *h, int32_t *grid_id);
 
 /* Queue a solve of grid grid_id with right-hand side b ([ny][nx], host or
- * device; copied before this call returns) writing the solution to x_out
- * ([ny][nx], host or device, written when the request completes). If
- * warm_start is nonzero the solve starts from the grid's last solution.
- * done (may be NULL) is called from the scheduler thread on completion. */
+ * device; copied into a device buffer of the grid's pool before this call
+ * returns) writing the solution to x_out ([ny][nx], host or device, written
+ * when the request completes). If warm_start is nonzero the solve starts from
+ * the grid's last solution. done (may be NULL) is called from the scheduler
+ * thread on completion. A new pool buffer counts against the HBM budget;
+ * PCG_EBUDGET if it does not fit (the request is not queued). */
 int solver_server_submit(pcg_server *s, int32_t grid_id, const double *b, double *x_out, int32_t warm_start,
                          void (*done)(void *user, const pcg_stats *stats), void *user, uint64_t *req_id);
 

@@ -227,7 +227,7 @@ static int build_loop_graph(LoopPlan &L) {
     for (size_t gi = 0; gi < L.groups.size(); ++gi) {
       const PlanGroup &G = L.groups[gi];
       if (G.n_units <= 0) continue;
-      const int guard = (pass == 0 && !guarded) ? 1 : 0;   // the first stencil launch of the body
+      const int guard = (pass == 1 && !guarded) ? 1 : 0;   // the first preconditioner launch of the body
       guarded = guarded || guard;
       params.push_back(kparams(L, G, pass == 0 ? (int)K1_ITER : (int)K2_ITER, 1, guard));
       void *args[] = {&params.back()};
@@ -264,6 +264,7 @@ int members_arm(LoopPlan &L, LaunchState *ls_host, int active, int max_launches,
   ls_host->cond = L.cond;
   ls_host->t0_ns = 0;
   ls_host->timed_out = 0;
+  ls_host->cond_cleared = 0;
   const char *e = getenv("PCG_LOOP_BUDGET_S");
   const double budget_s = (e && atof(e) > 0) ? atof(e) : 300.0;
   ls_host->budget_ns = (uint64_t)(budget_s * 1e9);
@@ -288,7 +289,7 @@ int members_loop(LoopPlan &L, LaunchState *ls_host, int max_launches, cudaStream
         for (size_t gi = 0; gi < L.groups.size(); ++gi) {
           const PlanGroup &G = L.groups[gi];
           if (G.n_units <= 0) continue;
-          const int guard = (pass == 0 && !guarded) ? 1 : 0;
+          const int guard = (pass == 1 && !guarded) ? 1 : 0;
           guarded = guarded || guard;
           int rc = launch(pass == 0 ? G.ks.k1 : G.ks.k2, G.n_units, G.ks.tb, pass == 0 ? G.ks.smem1 : G.ks.smem2,
                           kparams(L, G, pass == 0 ? (int)K1_ITER : (int)K2_ITER, 0, guard), s);
@@ -551,7 +552,7 @@ static int solve_members64(LoopPlan &L, LaunchState *ls_host, std::vector<Member
     CK(cudaMemcpyAsync(ls_host, L.ls, sizeof(LaunchState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (L.graph_ok) g_launches.fetch_add((uint64_t)std::max(ls_host->launches, 0) * L.body_kernels, std::memory_order_relaxed);
-    const bool overrun = ls_host->launches > ls_host->max_launches || ls_host->timed_out;
+    const bool overrun = (ls_host->stop && ls_host->active > 0) || ls_host->timed_out;
     active = 0;
     for (auto &m : M) {
       int err;
@@ -567,12 +568,89 @@ static int solve_members64(LoopPlan &L, LaunchState *ls_host, std::vector<Member
   return PCG_OK;
 }
 
+// Mixed precision, one refinement step of member m, after its binary64
+// residual r = b - A x has been computed and its state read back: either the
+// member is finished (returns true with final_status set and the state
+// retired on the device), or its binary32 inner solve is prepared -- the
+// right-hand side r scaled to unit root-mean-square by a power of two, x32
+// and the directions cleared, the inner state armed -- and false is returned.
+bool mixed_prepare_inner(Member &m, const pcg_opts &o, int budget, int outer, cudaStream_t s, int *err) {
+  *err = PCG_OK;
+  auto &P32 = m.h->p32;
+  SolveState &st = *m.st_host;
+  int fs = -1;
+  if (st.status != PCG_OK) fs = st.status;
+  else if (st.bzero) {
+    if (cudaMemsetAsync(m.h->p64.plane_start(m.h->p64.vec(0)), 0, m.h->p64.plane_elems * sizeof(double), s) != cudaSuccess)
+      *err = PCG_ECUDA;
+    m.relres64 = 0.0;
+    fs = PCG_OK;
+  } else {
+    m.relres64 = std::sqrt(st.rr) / std::sqrt(st.bb);
+    if (!(m.relres64 > o.rtol)) fs = PCG_OK;
+    else if (!std::isfinite(m.relres64)) fs = PCG_EBREAKDOWN;
+    else if (outer >= o.max_outer || m.inner_iters >= budget) fs = PCG_ENOTCONV;
+  }
+  SolveState st32{};
+  st32.status = PCG_OK;
+  if (fs >= 0) {
+    m.final_status = fs;
+    st.retired = 1; st.done = 1;
+    if (cudaMemcpyAsync(&m.h->p64.st->done, &st.done, sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(&m.h->p64.st->retired, &st.retired, sizeof(int32_t), cudaMemcpyHostToDevice, s) != cudaSuccess)
+      *err = PCG_ECUDA;
+    st32.done = 1; st32.retired = 1;
+  } else {
+    const double rms = std::sqrt(st.rr / std::max(m.h->G.n, 1));
+    m.scale = std::ldexp(1.0, -std::ilogb(rms > 0 ? rms : 1.0));
+    const GridDev<double> *g64 = m.h->p64.gd_dev;
+    const GridDev<float> *g32 = P32.gd_dev;
+    const Unit *un = m.h->p64.units_dev;
+    double sc = m.scale;
+    void *args[] = {(void *)&g64, (void *)&g32, (void *)&un, &sc};
+    const void *f = m.h->tx == 128 ? (const void *)k_residual_to_f32<128> : (const void *)k_residual_to_f32<64>;
+    if (m.h->p64.n_units > 0) {
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      if (cudaLaunchKernel(f, dim3(m.h->p64.n_units), dim3(m.h->tx), args, 0, s) != cudaSuccess) *err = PCG_ECUDA;
+    }
+    if (cudaMemsetAsync(P32.plane_start(P32.vec(0)), 0, P32.plane_elems * sizeof(float), s) != cudaSuccess) *err = PCG_ECUDA;
+    for (int v : {5, 6})
+      if (cudaMemsetAsync(P32.plane_start(P32.vec(v)), 0, P32.plane_elems * sizeof(float), s) != cudaSuccess) *err = PCG_ECUDA;
+    st32.rtol = o.inner_rtol;
+    st32.max_iter = std::max(1, budget - m.inner_iters);
+  }
+  *m.h->st32_host = st32;
+  if (cudaMemcpyAsync(P32.st, m.h->st32_host, sizeof(SolveState), cudaMemcpyHostToDevice, s) != cudaSuccess) *err = PCG_ECUDA;
+  if (*err) set_error("CUDA call failed in the refinement step");
+  return fs >= 0;
+}
+
+// Mixed precision: after member m's inner solve finished (its binary32 state
+// read back into st32_host and its last x32 update applied), x += e / scale
+// in binary64. Returns a pcg_status.
+int mixed_apply_correction(Member &m, cudaStream_t s) {
+  const SolveState &st32 = *m.h->st32_host;
+  m.inner_iters += st32.iter;
+  m.inner_solves += 1;
+  if (st32.status == PCG_EBREAKDOWN && st32.iter == 0) { m.final_status = PCG_EBREAKDOWN; return PCG_OK; }
+  const GridDev<double> *g64 = m.h->p64.gd_dev;
+  const GridDev<float> *g32 = m.h->p32.gd_dev;
+  const Unit *un = m.h->p64.units_dev;
+  double inv = 1.0 / m.scale;
+  void *args[] = {(void *)&g64, (void *)&g32, (void *)&un, &inv};
+  const void *f = m.h->tx == 128 ? (const void *)k_correct_f64<128> : (const void *)k_correct_f64<64>;
+  if (m.h->p64.n_units > 0) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    CK(cudaLaunchKernel(f, dim3(m.h->p64.n_units), dim3(m.h->tx), args, 0, s));
+  }
+  return PCG_OK;
+}
+
 // Mixed precision: iterative refinement in binary64 around binary32 PCG
 // solves. Each outer step computes the binary64 residual r = b - A x (the
 // binary64 stencil kernel), stops if ||r|| / ||b|| <= rtol, otherwise solves
 // A e = r in binary32 (r scaled by a power of two, inner tolerance
-// inner_rtol, dot products accumulated in binary64) and updates x += e in
-// binary64.
+// inner_rtol) and updates x += e in binary64.
 int solve_members_mixed(LoopPlan &L64, LoopPlan &L32, LaunchState *ls_host, std::vector<Member> &M,
                         const pcg_opts &o, cudaStream_t s) {
   int rc;
@@ -595,49 +673,16 @@ int solve_members_mixed(LoopPlan &L64, LoopPlan &L32, LaunchState *ls_host, std:
     CK(cudaStreamSynchronize(s));
     int inner = 0;
     for (auto &m : M) {
-      auto &P32 = m.h->p32;
-      SolveState st32{};
-      st32.status = PCG_OK; st32.done = 1; st32.retired = 1;
-      if (m.final_status < 0) {
-        SolveState &st = *m.st_host;
-        int fs = -1;
-        if (st.status != PCG_OK) fs = st.status;
-        else if (st.bzero) {
-          CK(cudaMemsetAsync(m.h->p64.plane_start(m.h->p64.vec(0)), 0, m.h->p64.plane_elems * sizeof(double), s));
-          m.relres64 = 0.0;
-          fs = PCG_OK;
-        } else {
-          m.relres64 = std::sqrt(st.rr) / std::sqrt(st.bb);
-          if (!(m.relres64 > o.rtol)) fs = PCG_OK;
-          else if (!std::isfinite(m.relres64)) fs = PCG_EBREAKDOWN;
-          else if (outer >= o.max_outer || m.inner_iters >= budget) fs = PCG_ENOTCONV;
-        }
-        if (fs >= 0) {
-          m.final_status = fs;
-          st.retired = 1; st.done = 1;
-          CK(cudaMemcpyAsync(&m.h->p64.st->done, &st.done, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-          CK(cudaMemcpyAsync(&m.h->p64.st->retired, &st.retired, sizeof(int32_t), cudaMemcpyHostToDevice, s));
-        } else {
-          // right-hand side of the inner solve: r scaled to unit root-mean-square
-          const double rms = std::sqrt(st.rr / std::max(m.h->G.n, 1));
-          m.scale = std::ldexp(1.0, -std::ilogb(rms > 0 ? rms : 1.0));
-          const GridDev<double> *g64 = m.h->p64.gd_dev;
-          const GridDev<float> *g32 = P32.gd_dev;
-          const Unit *un = m.h->p64.units_dev;
-          double sc = m.scale;
-          void *args[] = {(void *)&g64, (void *)&g32, (void *)&un, &sc};
-          const void *f = m.h->tx == 128 ? (const void *)k_residual_to_f32<128> : (const void *)k_residual_to_f32<64>;
-          if (m.h->p64.n_units > 0) CK(cudaLaunchKernel(f, dim3(m.h->p64.n_units), dim3(m.h->tx), args, 0, s));
-          CK(cudaMemsetAsync(P32.plane_start(P32.vec(0)), 0, P32.plane_elems * sizeof(float), s));
-          for (int v : {5, 6}) CK(cudaMemsetAsync(P32.plane_start(P32.vec(v)), 0, P32.plane_elems * sizeof(float), s));
-          st32.rtol = o.inner_rtol;
-          st32.max_iter = std::max(1, budget - m.inner_iters);
-          st32.done = 0; st32.retired = 0;
-          ++inner;
-        }
+      if (m.final_status >= 0) {
+        SolveState st32{};
+        st32.status = PCG_OK; st32.done = 1; st32.retired = 1;
+        *m.h->st32_host = st32;
+        CK(cudaMemcpyAsync(m.h->p32.st, m.h->st32_host, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+        continue;
       }
-      *m.h->st32_host = st32;
-      CK(cudaMemcpyAsync(P32.st, m.h->st32_host, sizeof(SolveState), cudaMemcpyHostToDevice, s));
+      int err;
+      if (!mixed_prepare_inner(m, o, budget, outer, s, &err)) ++inner;
+      if (err) return err;
     }
     if (inner == 0) continue;
     // binary32 inner solves of all of them together
@@ -651,34 +696,33 @@ int solve_members_mixed(LoopPlan &L64, LoopPlan &L32, LaunchState *ls_host, std:
     CK(cudaStreamSynchronize(s));
     if (L32.graph_ok) g_launches.fetch_add((uint64_t)std::max(ls_host->launches, 0) * L32.body_kernels, std::memory_order_relaxed);
     for (auto &m : M) {
-      if (m.final_status >= 0) continue;
-      const SolveState &st32 = *m.h->st32_host;
-      if (st32.retired) continue;
-      m.inner_iters += st32.iter;
-      m.inner_solves += 1;
-      if (st32.status == PCG_EBREAKDOWN && st32.iter == 0) { m.final_status = PCG_EBREAKDOWN; continue; }
-      // x += e / scale in binary64
-      const GridDev<double> *g64 = m.h->p64.gd_dev;
-      const GridDev<float> *g32 = m.h->p32.gd_dev;
-      const Unit *un = m.h->p64.units_dev;
-      double inv = 1.0 / m.scale;
-      void *args[] = {(void *)&g64, (void *)&g32, (void *)&un, &inv};
-      const void *f = m.h->tx == 128 ? (const void *)k_correct_f64<128> : (const void *)k_correct_f64<64>;
-      if (m.h->p64.n_units > 0) CK(cudaLaunchKernel(f, dim3(m.h->p64.n_units), dim3(m.h->tx), args, 0, s));
+      if (m.final_status >= 0 || m.h->st32_host->retired) continue;
+      if ((rc = mixed_apply_correction(m, s))) return rc;
     }
   }
   for (auto &m : M) if ((rc = member_store(m, s))) return rc;
   CK(cudaStreamSynchronize(s));
-  for (auto &m : M) {
-    if (!m.stats) continue;
-    m.stats->iters = m.inner_iters;
-    m.stats->outer_iters = m.inner_solves;
-    m.stats->status = m.final_status;
-    m.stats->replacements = 0;
-    m.stats->relres = m.relres64;
-    m.stats->true_relres = m.relres64;
-  }
+  for (auto &m : M) mixed_stats(m);
   return PCG_OK;
+}
+
+void mixed_stats(Member &m) {
+  if (!m.stats) return;
+  m.stats->iters = m.inner_iters;
+  m.stats->outer_iters = m.inner_solves;
+  m.stats->status = m.final_status;
+  m.stats->replacements = 0;
+  m.stats->relres = m.relres64;
+  m.stats->true_relres = m.relres64;
+}
+
+// Single-grid launches used by the server for the steps it runs per request.
+int single_launch(pcg_handle *h, bool f32, int which, int kind, cudaStream_t s) {
+  LoopPlan &L = f32 ? *h->plan32 : *h->plan64;
+  const PlanGroup &G = L.groups[0];
+  if (which == 1) return launch(G.ks.k1, G.n_units, G.ks.tb, G.ks.smem1, kparams(L, G, kind, 0, 0), s);
+  if (which == 2) return launch(G.ks.k2, G.n_units, G.ks.tb, G.ks.smem2, kparams(L, G, kind, 0, 0), s);
+  return launch(G.ks.fin, G.n_units, G.ks.tx, 0, kparams(L, G, 0, 0, 0), s);
 }
 
 std::string status_name(int s) {

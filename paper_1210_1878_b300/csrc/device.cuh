@@ -57,7 +57,8 @@ struct LaunchState {
   cudaGraphConditionalHandle cond;
   uint64_t t0_ns;          // device time of the first loop body (0 until then)
   uint64_t budget_ns;      // wall-clock cap on the loop (a runaway guard)
-  int32_t timed_out, pad;
+  int32_t timed_out;
+  int32_t cond_cleared;    // the loop condition has been cleared in this launch
 };
 
 template <typename T>

@@ -133,6 +133,11 @@ int ensure_f32(pcg_handle *h, cudaStream_t s);                                  
 int plan_build32(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls, cudaStream_t s);
 int solve_members_mixed(LoopPlan &L64, LoopPlan &L32, LaunchState *ls_host, std::vector<Member> &M,
                         const pcg_opts &o, cudaStream_t s);
+bool mixed_prepare_inner(Member &m, const pcg_opts &o, int budget, int outer, cudaStream_t s, int *err);
+int mixed_apply_correction(Member &m, cudaStream_t s);
+void mixed_stats(Member &m);
+// which: 1 stencil kernel, 2 preconditioner kernel, 0 final x update; kind: K1_* / K2_*
+int single_launch(pcg_handle *h, bool f32, int which, int kind, cudaStream_t s);
 int plan_build(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls, cudaStream_t s);
 std::string status_name(int s);
 void fill_opts(const pcg_opts *o, pcg_opts &out);

@@ -105,22 +105,52 @@ struct Pat<PCG_PAT_BAND_T, Q> {
 };
 
 __host__ __device__ constexpr int round_up_c(int v, int a) { return (v + a - 1) / a * a; }
+__host__ __device__ constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
 
-// Exact widening to binary64 for the dot-product accumulators. For binary32
-// values it assembles the binary64 bit pattern from the binary32 fields with
-// integer operations (IEEE 754: sign kept, exponent re-biased by 1023 - 127,
-// 23-bit fraction shifted into the top of the 52-bit fraction), so the
-// accumulation in binary64 costs no conversion on the slow FP64 pipe of this
-// GPU. Zero, subnormal, infinite and NaN inputs take the hardware conversion.
+// Exact widening of binary32 to binary64 with integer operations only (IEEE
+// 754 formats: sign kept; exponent re-biased by 1023 - 127; the 23-bit
+// fraction moved to the top of the 52-bit fraction; subnormals normalised by a
+// leading-zero count; infinities and NaNs keep their fraction bits). On this
+// GPU the hardware conversion runs on the slow FP64 pipe, which the binary32
+// kernels must leave alone.
 __device__ __forceinline__ double to_f64(double v) { return v; }
 __device__ __forceinline__ double to_f64(float v) {
   const uint32_t u = __float_as_uint(v);
-  const uint32_t e = (u >> 23) & 0xFFu;
-  if (e == 0u || e == 0xFFu) return (double)v;
-  const uint32_t hi = (u & 0x80000000u) | ((e + (1023u - 127u)) << 20) | ((u & 0x7FFFFFu) >> 3);
-  const uint32_t lo = (u & 0x7u) << 29;
-  return __hiloint2double((int)hi, (int)lo);
+  const uint32_t sgn = u & 0x80000000u, e = (u >> 23) & 0xFFu;
+  uint32_t f = u & 0x7FFFFFu, E;
+  if (e == 0xFFu) {
+    E = 0x7FFu;
+  } else if (e != 0u) {
+    E = e + (1023u - 127u);
+  } else if (f == 0u) {
+    E = 0u;
+  } else {
+    const uint32_t top = 31u - (uint32_t)__clz((int)f);   // bit of the leading one, < 23
+    E = top + 874u;                                         // value = f * 2^-149
+    f = (f << (23u - top)) & 0x7FFFFFu;
+  }
+  return __hiloint2double((int)(sgn | (E << 20) | (f >> 3)), (int)(f << 29));
 }
+
+// Dot-product term accumulation. binary64 kernels accumulate in binary64.
+// binary32 kernels keep a binary32 partial sum per thread over the rows of
+// its column in one work unit (at most a unit's height of terms); the partial
+// is widened exactly and added into the binary64 accumulator when the unit is
+// done, so every long accumulation is in binary64.
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+  __device__ __forceinline__ double total() const { return v; }
+};
+template <>
+struct DotAcc<float> {
+  float v = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) { v = fmaf(a, b, v); }
+  __device__ __forceinline__ double total() const { return to_f64(v); }
+};
 
 // ------------------------------------------------------------ stores
 // Store one value of column `col` (0 <= col < nx) of a row, together with its
@@ -185,13 +215,33 @@ __device__ __forceinline__ bool grid_reduce2(double &sa, double &sb, double *par
   return true;
 }
 
+// End the conditional loop graph after the current body: exactly one thread
+// per graph launch sets the condition (concurrent settings are not allowed).
+__device__ __forceinline__ void clear_loop_condition(LaunchState *ls, const KParams &p) {
+  if (p.use_cond && atomicExch(&ls->cond_cleared, 1) == 0) cudaGraphSetConditional(ls->cond, 0);
+}
+
 __device__ __forceinline__ void grid_finished(SolveState *st, LaunchState *ls, int status, bool may_set_cond,
                                              const KParams &p) {
   if (status != PCG_OK) atomicCAS(&st->status, PCG_OK, status);
   st->done = 1;
   __threadfence();
   const int prev = atomicSub(&ls->active, 1);
-  if (prev == 1 && may_set_cond && p.use_cond) cudaGraphSetConditional(ls->cond, 0);
+  if (prev == 1 && may_set_cond) clear_loop_condition(ls, p);
+}
+
+// Loop guard, run by one thread of the first preconditioner launch of each
+// loop body (the body's last kernel, so a body always runs whole): counts the
+// bodies and ends the loop once all grids are done, after max_launches
+// bodies, or when the wall-clock budget is spent.
+__device__ __forceinline__ void loop_guard(LaunchState *ls, const KParams &p) {
+  const int l = atomicAdd(&ls->launches, 1) + 1;
+  const uint64_t now = global_ns();
+  if (ls->t0_ns == 0) ls->t0_ns = now;
+  const bool late = now - ls->t0_ns > ls->budget_ns;
+  if (late) ls->timed_out = 1;
+  if (l >= ls->max_launches || late) ls->stop = 1;
+  if (l >= ls->max_launches || late || atomicAdd(&ls->active, 0) == 0) clear_loop_condition(ls, p);
 }
 
 __device__ __forceinline__ void flag_timeout(SolveState *st) { atomicCAS(&st->status, PCG_OK, PCG_ETIMEOUT); }
@@ -260,7 +310,7 @@ __device__ __forceinline__ int produce_rows(const RowCopy &c, unsigned char *rin
                                             bool skip_first, uint64_t timeout_ns, const volatile int *abort) {
   int last = mlo - 1;
   for (int n = mlo; n <= mhi; ++n) {
-    const int slot = (n - mlo) % NST, fill = (n - mlo) / NST;
+    const int slot = (NST & (NST - 1)) == 0 ? ((n - mlo) & (NST - 1)) : ((n - mlo) % NST), fill = (n - mlo) / NST;
     if (fill > 0) {
       bool ok = true;
       if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(&empty[slot], (uint32_t)((fill - 1) & 1), timeout_ns);
@@ -288,9 +338,8 @@ struct K1Geom {
   static constexpr int WS = TX + 2 * H;              // s, d_old / x / v: [i0-H, i0+TX+H)
   static constexpr int WE = TX + H;                  // c_e: [i0-H, i0+TX)
   static constexpr int WT = TX;                      // c_n, a, x / b
-  static constexpr int PF = sizeof(T) == 8 ? 3 : 4;  // rows streamed ahead
-  static constexpr int NST = 4 + PF;                 // ring slots: rows m-3..m live
-  static constexpr int NDN = 4;                      // rows of d' kept
+  static constexpr int NST = 8;                      // ring slots (a power of two): rows m-3..m live, 4 ahead
+  static constexpr int NDN = 4;                      // rows of d' kept (a power of two)
   static constexpr int NT = TX + 32;                 // compute threads + producer warp
   static constexpr int OFF_S = 0, OFF_D = WS, OFF_E = 2 * WS, OFF_N = 2 * WS + WE, OFF_A = OFF_N + WT,
                        OFF_X = OFF_A + WT, SLOT = OFF_X + WT;
@@ -319,18 +368,6 @@ __global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
   const int kind = p.kind;
   const int tid = threadIdx.x;
 
-  if (p.guard && blockIdx.x == 0 && tid == 0) {
-    // loop exit and runaway guard (count and wall clock) of the loop graph
-    const int l = atomicAdd(&ls->launches, 1) + 1;
-    const uint64_t now = global_ns();
-    if (ls->t0_ns == 0) ls->t0_ns = now;
-    const bool late = now - ls->t0_ns > ls->budget_ns;
-    if (late) ls->timed_out = 1;
-    if (l > ls->max_launches || late || atomicAdd(&ls->active, 0) == 0) {
-      ls->stop = 1;
-      if (p.use_cond) cudaGraphSetConditional(ls->cond, 0);
-    }
-  }
   if ((kind == K1_ITER || kind == K1_RESID_INIT) && *(volatile int32_t *)&st->done) return;
   if (kind == K1_RESID_CHECK && *(volatile int32_t *)&st->retired) return;
 
@@ -350,6 +387,7 @@ __global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
   __syncthreads();
 
   double acc0 = 0.0, acc1 = 0.0;
+  DotAcc<T> dot0, dot1;
   if (tid >= TX) {
     // ---- producer warp
     const int lane = tid - TX;
@@ -381,10 +419,10 @@ __global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
     for (int m = mlo; m <= mhi + 1; ++m) {
       bool got = true;
       if (m <= mhi) {
-        const int slot = (m - mlo) % G::NST;
+        const int slot = (m - mlo) & (G::NST - 1);
         got = mbar_wait_bounded(&full[slot], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
         const T *sl = ring + (size_t)slot * G::SLOT;
-        T *dnm = dn + (size_t)((m + 8) % G::NDN) * G::WDN;
+        T *dnm = dn + (size_t)((m + 8) & (G::NDN - 1)) * G::WDN;
         // d' on row m over columns [i0-1, i0+TX+1)
         for (int c = tid; c < G::WDN; c += TX) {
           const int k = c - 1 + G::H;
@@ -397,11 +435,11 @@ __global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
       if (r >= j0 && r < rend) {
         const int col = i0 + tid;
         if (col < nx) {
-          const T *slr = ring + (size_t)((r - mlo) % G::NST) * G::SLOT;
-          const T *sls = ring + (size_t)((r - 1 - mlo) % G::NST) * G::SLOT;
-          const T *dr = dn + (size_t)((r + 8) % G::NDN) * G::WDN;
-          const T *ds = dn + (size_t)((r - 1 + 8) % G::NDN) * G::WDN;
-          const T *dnn = dn + (size_t)((r + 1 + 8) % G::NDN) * G::WDN;
+          const T *slr = ring + (size_t)((r - mlo) & (G::NST - 1)) * G::SLOT;
+          const T *sls = ring + (size_t)((r - 1 - mlo) & (G::NST - 1)) * G::SLOT;
+          const T *dr = dn + (size_t)((r + 8) & (G::NDN - 1)) * G::WDN;
+          const T *ds = dn + (size_t)((r - 1 + 8) & (G::NDN - 1)) * G::WDN;
+          const T *dnn = dn + (size_t)((r + 1 + 8) & (G::NDN - 1)) * G::WDN;
           const T c_ctr = dr[tid + 1];
           T av = -sls[G::OFF_N + tid] * ds[tid + 1];
           av = fma(-slr[G::OFF_E + G::H + tid - 1], dr[tid], av);
@@ -414,15 +452,15 @@ __global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
             store_dup(d_out + ro, col, nx, c_ctr);
             store_dup(x_out + ro, col, nx, xv);
             store_dup(q_out + ro, col, nx, av);
-            acc0 = fma(to_f64(c_ctr), to_f64(av), acc0);
+            dot0.add(c_ctr, av);
           } else if (kind == K1_SPMV) {
             store_dup(q_out + ro, col, nx, av);
           } else {
             const T bv = slr[G::OFF_X + tid];
             const T rv = bv - av;
             store_dup(r_out + ro, col, nx, rv);
-            acc0 = fma(to_f64(rv), to_f64(rv), acc0);
-            acc1 = fma(to_f64(bv), to_f64(bv), acc1);
+            dot0.add(rv, rv);
+            dot1.add(bv, bv);
           }
         }
       }
@@ -432,15 +470,17 @@ __global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
       }
       if (m <= mhi) consumed = m;
       // row m-3 is finished: its slot may be refilled
-      if (tid == 0 && m - 3 >= mlo && m - 3 + G::NST <= mhi) mbar_arrive(&empty[(m - 3 - mlo) % G::NST]);
+      if (tid == 0 && m - 3 >= mlo && m - 3 + G::NST <= mhi) mbar_arrive(&empty[(m - 3 - mlo) & (G::NST - 1)]);
     }
     if (tid == 0) ctl[2] = consumed;
+    acc0 = dot0.total();
+    acc1 = dot1.total();
   }
   __syncthreads();
   if (tid == 0 && ctl[2] < ctl[1]) {
     // the compute threads gave up: wait (bounded) for the rows still in flight
     for (int m = ctl[2] + 1; m <= ctl[1]; ++m)
-      mbar_wait_bounded(&full[(m - mlo) % G::NST], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
+      mbar_wait_bounded(&full[(m - mlo) & (G::NST - 1)], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
   }
   if (kind == K1_SPMV) return;
   if (grid_reduce2<NT>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt1, red, flag)) {
@@ -482,13 +522,16 @@ struct K2Geom {
   static constexpr int WR = TX + 2 * HR, WZ = TX + 2 * HZ;
   static constexpr int WRC = TX + 4 * R;             // r' computed on [i0-2R, i0+TX+2R)
   static constexpr int WTC = TX + 2 * R;             // t computed on [i0-R, i0+TX+R)
-  static constexpr int NRN = LD + 3;                 // rows of r' kept (m-2-LD .. m)
-  static constexpr int NTT = LD + 2;                 // rows of t kept (m-2-LD .. m-1)
+  static constexpr int NRN = pow2_at_least(LD + 3);  // rows of r' kept (m-2-LD .. m)
+  static constexpr int NTT = pow2_at_least(LD + 2);  // rows of t kept (m-2-LD .. m-1)
   // rows streamed ahead: binary64 is bound by the FP64 pipe, so shared memory
   // goes to CTAs (latency hiding for the FP64 work); binary32 is bound by
   // HBM, so it goes to rows in flight
-  static constexpr int PF = sizeof(T) == 8 ? 1 : 2;
-  static constexpr int NST = LD + 3 + PF;            // ring slots: rows m-2-LD .. m live
+  // ring slots: rows m-2-LD .. m live plus rows in flight. binary64 is bound
+  // by the FP64 pipe, so its shared memory goes to CTAs (one row ahead);
+  // binary32 is bound by HBM, so it keeps more rows in flight.
+  static constexpr int NST = sizeof(T) == 8 ? LD + 4 : pow2_at_least(LD + 5);
+  __device__ static constexpr int slot(int x) { return (NST & (NST - 1)) == 0 ? (x & (NST - 1)) : (x % NST); }
   static constexpr int NT = TX + 32;                 // compute threads + producer warp
   static constexpr int OFF_R = 0, OFF_Q = WR, OFF_Z = 2 * WR, OFF_DI = 2 * WR + NZ * WZ, SLOT = OFF_DI + WZ;
   static constexpr size_t SMEM =
@@ -517,7 +560,7 @@ __global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
   const int kind = p.kind;
   const int tid = threadIdx.x;
 
-  if (kind == K2_ITER && p.use_cond && *(volatile int32_t *)&ls->stop) return;
+  if (p.guard && blockIdx.x == 0 && tid == 0) loop_guard(ls, p);
   if (kind != K2_APPLY && *(volatile int32_t *)&st->done) return;
 
   const int nx = gdp->nx, ny = gdp->ny, pitch = gdp->pitch, ty = gdp->ty;
@@ -536,6 +579,7 @@ __global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
   __syncthreads();
 
   double acc0 = 0.0, acc1 = 0.0;
+  DotAcc<T> dot0, dot1;
   if (tid >= TX) {
     // ---- producer warp
     const int lane = tid - TX;
@@ -562,10 +606,10 @@ __global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
       bool got = true;
       // r' on row m over [i0-2R, i0+TX+2R)
       if (m <= mhi) {
-        const int slot = (m - mlo) % G::NST;
+        const int slot = G::slot(m - mlo);
         got = mbar_wait_bounded(&full[slot], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
         const T *sl = ring + (size_t)slot * G::SLOT;
-        T *rnm = rn + (size_t)((m + 8) % G::NRN) * G::WRC;
+        T *rnm = rn + (size_t)((m + 8) & (G::NRN - 1)) * G::WRC;
         for (int c = tid; c < G::WRC; c += TX) {
           const int k = c + G::HR - 2 * R;
           T v = sl[G::OFF_R + k];
@@ -576,9 +620,9 @@ __global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
       // t = D^-1 (Z^T r') on row mt = m - 1 over [i0-R, i0+TX+R)
       const int mt = m - 1;
       if (mt >= j0 && mt <= mhi) {
-        const T *sl = ring + (size_t)((mt - mlo) % G::NST) * G::SLOT;
-        const T *rnt = rn + (size_t)((mt + 8) % G::NRN) * G::WRC;
-        T *tm = tt + (size_t)((mt + 8) % G::NTT) * G::WTC;
+        const T *sl = ring + (size_t)(G::slot(mt - mlo)) * G::SLOT;
+        const T *rnt = rn + (size_t)((mt + 8) & (G::NRN - 1)) * G::WRC;
+        T *tm = tt + (size_t)((mt + 8) & (G::NTT - 1)) * G::WTC;
         for (int c = tid; c < G::WTC; c += TX) {
           T acc = (T)0;
           if (mt < ny) {
@@ -586,7 +630,7 @@ __global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
             acc = rnt[c + R];
 #pragma unroll
             for (int s = 0; s < NZ; ++s) {
-              const T *rrow = rn + (size_t)((mt + P::dy(s) + 8) % G::NRN) * G::WRC;
+              const T *rrow = rn + (size_t)((mt + P::dy(s) + 8) & (G::NRN - 1)) * G::WRC;
               acc = fma(sl[G::OFF_Z + s * G::WZ + kz], rrow[c + R + P::dx(s)], acc);
             }
             if (edge) {
@@ -606,13 +650,13 @@ __global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
       if (r >= j0 && r < rend) {
         const int col = i0 + tid;
         if (col < nx) {
-          const T *tr = tt + (size_t)((r + 8) % G::NTT) * G::WTC;
+          const T *tr = tt + (size_t)((r + 8) & (G::NTT - 1)) * G::WTC;
           T acc = tr[tid + R];
 #pragma unroll
           for (int s = 0; s < NZ; ++s) {
             const int rowz = r - P::dy(s);           // row of the column holding Z[(col,r), that column]
-            const T *slz = ring + (size_t)((rowz - mlo) % G::NST) * G::SLOT;
-            const T *trow = tt + (size_t)((rowz + 8) % G::NTT) * G::WTC;
+            const T *slz = ring + (size_t)(G::slot(rowz - mlo)) * G::SLOT;
+            const T *trow = tt + (size_t)((rowz + 8) & (G::NTT - 1)) * G::WTC;
             acc = fma(slz[G::OFF_Z + s * G::WZ + tid - P::dx(s) + G::HZ], trow[tid + R - P::dx(s)], acc);
           }
           if (edge) {
@@ -622,13 +666,13 @@ __global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
               if (col == target) acc = fma(zwrap[(size_t)r * NW + w], tr[tid + R - P::wdx(w)], acc);
             }
           }
-          const T *rnr = rn + (size_t)((r + 8) % G::NRN) * G::WRC;
+          const T *rnr = rn + (size_t)((r + 8) & (G::NRN - 1)) * G::WRC;
           const T rv = rnr[tid + 2 * R];
           const size_t ro = (size_t)r * pitch;
           store_dup(s_out + ro, col, nx, acc);
           if (kind != K2_APPLY) store_dup(rout + ro, col, nx, rv);
-          acc0 = fma(to_f64(acc), to_f64(rv), acc0);
-          acc1 = fma(to_f64(rv), to_f64(rv), acc1);
+          dot0.add(acc, rv);
+          dot1.add(rv, rv);
         }
       }
       if (!compute_sync_and<TX>(got)) {
@@ -637,14 +681,16 @@ __global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
       }
       if (m <= mhi) consumed = m;
       // row m-2-LD is finished: its slot may be refilled
-      if (tid == 0 && m - 2 - LD >= mlo && m - 2 - LD + G::NST <= mhi) mbar_arrive(&empty[(m - 2 - LD - mlo) % G::NST]);
+      if (tid == 0 && m - 2 - LD >= mlo && m - 2 - LD + G::NST <= mhi) mbar_arrive(&empty[G::slot(m - 2 - LD - mlo)]);
     }
     if (tid == 0) ctl[2] = consumed;
+    acc0 = dot0.total();
+    acc1 = dot1.total();
   }
   __syncthreads();
   if (tid == 0 && ctl[2] < ctl[1]) {
     for (int m = ctl[2] + 1; m <= ctl[1]; ++m)
-      mbar_wait_bounded(&full[(m - mlo) % G::NST], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
+      mbar_wait_bounded(&full[G::slot(m - mlo)], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
   }
   if (kind == K2_APPLY) return;
   if (grid_reduce2<NT>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt2, red, flag)) {

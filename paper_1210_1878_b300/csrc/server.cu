@@ -40,7 +40,7 @@ namespace {
 struct Request {
   uint64_t id = 0;
   int grid = 0;
-  std::vector<double> b;           // copy of the right-hand side (host)
+  double *b = nullptr;             // device copy of the right-hand side (from the grid's buffer pool)
   double *x_out = nullptr;
   bool warm = false;
   void (*done)(void *, const pcg_stats *) = nullptr;
@@ -55,6 +55,8 @@ struct GridEntry {
   pcg_handle *h = nullptr;
   bool busy = false;
   bool has_solution = false;
+  std::vector<double *> pool;      // free right-hand-side buffers of this grid's size
+  size_t buffers = 0;              // buffers allocated for this grid
 };
 
 }  // namespace
@@ -82,21 +84,29 @@ struct pcg_server {
 };
 
 void pcg_server::run() {
+  // A request moves through phases. binary64: START (init kernels) -> ITER
+  // (advanced with the others, chunk by chunk) -> its x update and true
+  // residual, then a restart from the true residual or the end. Mixed: START
+  // (binary64 residual; the end, or a binary32 inner solve set up) -> ITER
+  // (the inner solve, advanced with the others) -> its last x32 update and the
+  // binary64 correction -> START again.
+  enum { START = 0, ITER = 1 };
   struct Active {
     std::shared_ptr<Request> r;
     Member m;
-    SolveState *st_host = nullptr;
+    int phase = START;
+    int outer = 0;
   };
   std::vector<Active> active;
   std::unique_ptr<LoopPlan> plan;
   bool plan_dirty = true;
   pcg_opts o;
   fill_opts(&opts.solve, o);
+  const bool mixed = o.prec == PCG_MIXED;
   const int chunk = std::max(1, opts.chunk_iters);
   auto finish = [&](Active &a, int status) {
     a.m.final_status = status;
-    member_stats(a.m);
-    a.r->stats = a.m.stats ? *a.m.stats : pcg_stats{};
+    if (mixed) mixed_stats(a.m); else member_stats(a.m);
     a.r->stats.status = status;
     a.r->t_done = Clock::now();
     a.r->stats.seconds = std::chrono::duration<double>(a.r->t_done - a.r->t_submit).count();
@@ -105,12 +115,19 @@ void pcg_server::run() {
     a.r->status = status;
     a.r->finished = true;
     grids[a.r->grid].busy = false;
+    if (a.r->b) { grids[a.r->grid].pool.push_back(a.r->b); a.r->b = nullptr; }
     if (status == PCG_OK) grids[a.r->grid].has_solution = true;
     if (status == PCG_OK) ++completed; else ++failed;
     lat_ms.push_back(a.r->stats.seconds * 1e3);
     t_last = a.r->t_done;
     --in_flight;
     cv_done.notify_all();
+  };
+  // the final x of a finished request goes to its output buffer
+  auto retire = [&](Active &a) {
+    int rc = member_store(a.m, stream);
+    if (!rc && cudaStreamSynchronize(stream) != cudaSuccess) rc = PCG_ECUDA;
+    finish(a, rc ? rc : a.m.final_status);
   };
 
   for (;;) {
@@ -128,82 +145,121 @@ void pcg_server::run() {
         it = queue.erase(it);
       }
     }
-    // 1. admission: load inputs and run the init kernels of each new request
+    // admission: inputs on the device (the warm start keeps the grid's last x)
     for (auto &r : admitted) {
       Active a;
       a.r = r;
       a.m.h = grids[r->grid].h;
-      a.m.b = r->b.data();
+      a.m.b = r->b;
       a.m.x = r->x_out;
       a.m.stats = &r->stats;
       a.m.st_host = a.m.h->st_host;
       pcg_opts ro = o;
       ro.use_x0 = (r->warm && grids[r->grid].has_solution) ? 1 : 0;
-      int rc = member_load(a.m, ro, false, stream);
-      LoopPlan *single = nullptr;
-      if (!rc) rc = plan_single(a.m.h);
-      if (!rc) {
-        single = a.m.h->plan64.get();
-        rc = members_arm(*single, a.m.h->ls_host, 1, 1, stream);
-      }
-      if (!rc) rc = members_init(*single, stream);
+      int rc = plan_single(a.m.h);
+      if (!rc && mixed) rc = ensure_f32(a.m.h, stream);
+      if (!rc) rc = member_load(a.m, ro, false, stream);
       if (rc) { finish(a, rc); continue; }
+      a.m.inner_iters = 0; a.m.inner_solves = 0; a.m.relres64 = 0.0;
       active.push_back(std::move(a));
-      plan_dirty = true;
     }
     if (active.empty()) continue;
-    // states after init (some may already be done)
-    for (auto &a : active) cudaMemcpyAsync(a.m.st_host, a.m.h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream);
+    // START phase: per-request setup steps
+    const int budget_cap = o.max_iter;
+    std::vector<Active> next;
+    for (auto &a : active) {
+      if (a.phase != START) { next.push_back(std::move(a)); continue; }
+      pcg_handle *h = a.m.h;
+      int rc = PCG_OK;
+      if (!mixed) {
+        rc = members_arm(*h->plan64, h->ls_host, 1, 1, stream);
+        if (!rc) rc = single_launch(h, false, 1, K1_RESID_INIT, stream);
+        if (!rc) rc = single_launch(h, false, 2, K2_INIT, stream);
+        if (rc) { finish(a, rc); continue; }
+        a.phase = ITER;
+        plan_dirty = true;
+        next.push_back(std::move(a));
+        continue;
+      }
+      rc = members_arm(*h->plan64, h->ls_host, 1, 1, stream);
+      if (!rc) rc = single_launch(h, false, 1, K1_RESID_INIT, stream);
+      if (!rc && cudaMemcpyAsync(a.m.st_host, h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream) != cudaSuccess) rc = PCG_ECUDA;
+      if (!rc && cudaStreamSynchronize(stream) != cudaSuccess) rc = PCG_ECUDA;
+      if (rc) { finish(a, rc); continue; }
+      const int budget = budget_cap > 0 ? budget_cap : std::max(h->G.n, 1);
+      int err = PCG_OK;
+      const bool over = mixed_prepare_inner(a.m, o, budget, a.outer, stream, &err);
+      if (err) { finish(a, err); continue; }
+      if (over) { retire(a); continue; }
+      rc = members_arm(*h->plan32, h->ls_host, 1, 1, stream);
+      if (!rc) rc = single_launch(h, true, 1, K1_RESID_INIT, stream);
+      if (!rc) rc = single_launch(h, true, 2, K2_INIT, stream);
+      if (rc) { finish(a, rc); continue; }
+      a.outer += 1;
+      a.phase = ITER;
+      plan_dirty = true;
+      next.push_back(std::move(a));
+    }
+    active.swap(next);
+    if (active.empty()) continue;
+    // states of the iterating requests (some may be done already)
+    auto state_of = [&](Active &a) -> SolveState & { return mixed ? *a.m.h->st32_host : *a.m.st_host; };
+    auto dev_state = [&](Active &a) { return mixed ? a.m.h->p32.st : a.m.h->p64.st; };
+    for (auto &a : active) cudaMemcpyAsync(&state_of(a), dev_state(a), sizeof(SolveState), cudaMemcpyDeviceToHost, stream);
     if (cudaStreamSynchronize(stream) != cudaSuccess) {
       for (auto &a : active) finish(a, PCG_ECUDA);
       active.clear();
       continue;
     }
     int n_iter = 0;
-    for (auto &a : active) n_iter += (!a.m.st_host->done && a.m.st_host->status == PCG_OK) ? 1 : 0;
-    // 2. advance all together by up to `chunk` iterations
+    for (auto &a : active) n_iter += (a.phase == ITER && !state_of(a).done) ? 1 : 0;
+    // advance every iterating request together by up to `chunk` iterations
     if (n_iter > 0) {
       if (plan_dirty) {
         plan = std::make_unique<LoopPlan>();
         std::vector<pcg_handle *> hs;
         for (auto &a : active) hs.push_back(a.m.h);
-        int rc = plan_build(*plan, hs.data(), (int)hs.size(), true, ls_dev, stream);
+        int rc = mixed ? plan_build32(*plan, hs.data(), (int)hs.size(), true, ls_dev, stream)
+                       : plan_build(*plan, hs.data(), (int)hs.size(), true, ls_dev, stream);
         if (rc) { for (auto &a : active) finish(a, rc); active.clear(); continue; }
         plan_dirty = false;
       }
       int rc = members_arm(*plan, ls_host, n_iter, chunk, stream);
       if (!rc) rc = members_loop(*plan, ls_host, chunk, stream);
-      for (auto &a : active) cudaMemcpyAsync(a.m.st_host, a.m.h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream);
+      for (auto &a : active) cudaMemcpyAsync(&state_of(a), dev_state(a), sizeof(SolveState), cudaMemcpyDeviceToHost, stream);
       if (rc || cudaStreamSynchronize(stream) != cudaSuccess) {
         for (auto &a : active) finish(a, PCG_ECUDA);
         active.clear();
         continue;
       }
     }
-    // 3. close finished requests: x update, true residual, restart or retire
+    // requests whose iteration ended
     std::vector<Active> still;
     for (auto &a : active) {
-      const SolveState &st = *a.m.st_host;
+      const SolveState &st = state_of(a);
       if (!st.done && st.status == PCG_OK) { still.push_back(std::move(a)); continue; }
-      LoopPlan *single = a.m.h->plan64.get();
-      int rc = members_close(*single, stream);
-      if (!rc && cudaMemcpyAsync(a.m.st_host, a.m.h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream) != cudaSuccess) rc = PCG_ECUDA;
-      if (!rc && cudaStreamSynchronize(stream) != cudaSuccess) rc = PCG_ECUDA;
-      if (rc) { finish(a, rc); plan_dirty = true; continue; }
-      int err = PCG_OK;
-      const bool again = member_decide(a.m, o, false, stream, &err);
-      if (err) { finish(a, err); plan_dirty = true; continue; }
-      if (again) {
-        rc = members_arm(*single, a.m.h->ls_host, 1, 1, stream);
-        if (!rc) rc = members_init(*single, stream);
-        if (rc) { finish(a, rc); plan_dirty = true; continue; }
+      pcg_handle *h = a.m.h;
+      plan_dirty = true;
+      int rc;
+      if (mixed) {
+        // last x32 update, then the binary64 correction; back to START
+        rc = single_launch(h, true, 0, 0, stream);
+        if (!rc) rc = mixed_apply_correction(a.m, stream);
+        if (rc) { finish(a, rc); continue; }
+        if (a.m.final_status >= 0) { retire(a); continue; }
+        a.phase = START;
         still.push_back(std::move(a));
         continue;
       }
-      rc = member_store(a.m, stream);
+      rc = members_close(*h->plan64, stream);
+      if (!rc && cudaMemcpyAsync(a.m.st_host, h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream) != cudaSuccess) rc = PCG_ECUDA;
       if (!rc && cudaStreamSynchronize(stream) != cudaSuccess) rc = PCG_ECUDA;
-      finish(a, rc ? rc : a.m.final_status);
-      plan_dirty = true;
+      if (rc) { finish(a, rc); continue; }
+      int err = PCG_OK;
+      const bool again = member_decide(a.m, o, false, stream, &err);
+      if (err) { finish(a, err); continue; }
+      if (again) { a.phase = START; still.push_back(std::move(a)); continue; }
+      retire(a);
     }
     active.swap(still);
   }
@@ -250,24 +306,46 @@ int solver_server_register(pcg_server *s, pcg_handle *h, int32_t *grid_id) {
 int solver_server_submit(pcg_server *s, int32_t grid_id, const double *b, double *x_out, int32_t warm_start,
                          void (*done)(void *, const pcg_stats *), void *user, uint64_t *req_id) {
   if (!s || !b || !x_out) { set_error("NULL argument"); return PCG_EINVAL; }
-  pcg_handle *h;
+  auto r = std::make_shared<Request>();
+  size_t n = 0;
   {
+    // a right-hand-side buffer from the grid's pool; a new one only if the
+    // HBM budget (registered grids + buffers) allows it
     std::lock_guard<std::mutex> lk(s->mu);
     if (grid_id < 0 || grid_id >= (int)s->grids.size()) { set_error("unknown grid id"); ++s->rejected; return PCG_EINVAL; }
-    h = s->grids[grid_id].h;
+    GridEntry &g = s->grids[grid_id];
+    n = (size_t)g.h->G.nx * g.h->G.ny;
+    if (!g.pool.empty()) {
+      r->b = g.pool.back();
+      g.pool.pop_back();
+    } else {
+      if (s->hbm_used + n * sizeof(double) > s->opts.hbm_budget_bytes) {
+        ++s->rejected;
+        set_error("no right-hand-side buffer fits in the HBM budget");
+        return PCG_EBUDGET;
+      }
+      if (cudaMalloc(&r->b, n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        ++s->rejected;
+        set_error("device allocation of a right-hand-side buffer failed");
+        return PCG_ENOMEM;
+      }
+      s->hbm_used += n * sizeof(double);
+      g.buffers += 1;
+    }
   }
-  auto r = std::make_shared<Request>();
   r->grid = grid_id;
   r->x_out = x_out;
   r->warm = warm_start != 0;
   r->done = done;
   r->user = user;
-  const size_t n = (size_t)h->G.nx * h->G.ny;
-  r->b.resize(n);
-  if (is_device_ptr(b)) {
-    CK(cudaMemcpy(r->b.data(), b, n * sizeof(double), cudaMemcpyDeviceToHost));
-  } else {
-    std::memcpy(r->b.data(), b, n * sizeof(double));
+  // the caller may reuse b as soon as this returns
+  if (cudaMemcpy(r->b, b, n * sizeof(double), cudaMemcpyDefault) != cudaSuccess) {
+    cudaGetLastError();
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->grids[grid_id].pool.push_back(r->b);
+    set_error("copy of the right-hand side failed");
+    return PCG_ECUDA;
   }
   std::lock_guard<std::mutex> lk(s->mu);
   r->t_submit = Clock::now();
@@ -306,6 +384,7 @@ int solver_server_cancel(pcg_server *s, uint64_t req_id) {
   if (it == s->queue.end()) { set_error("request is not queued (running, finished or unknown)"); return PCG_EINVAL; }
   s->queue.erase(it);
   auto r = s->reqs[req_id];
+  if (r->b) { s->grids[r->grid].pool.push_back(r->b); r->b = nullptr; }
   r->status = PCG_ECANCELLED;
   r->stats.status = PCG_ECANCELLED;
   r->finished = true;
@@ -359,6 +438,10 @@ void solver_server_destroy(pcg_server *s) {
   }
   if (s->th.joinable()) s->th.join();
   cudaStreamSynchronize(s->stream);
+  for (auto &g : s->grids)
+    for (double *p : g.pool) cudaFree(p);
+  for (auto &kv : s->reqs)
+    if (kv.second->b) cudaFree(kv.second->b);
   cudaStreamDestroy(s->stream);
   cudaFree(s->ls_dev);
   cudaFreeHost(s->ls_host);
