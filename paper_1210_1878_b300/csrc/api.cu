@@ -34,7 +34,8 @@ static KernelSet make_set() {
   k.smem1 = K1Geom<T, TX>::SMEM;
   k.smem2 = K2Geom<T, TX, P>::SMEM;
   k.tx = TX;
-  k.tb = TX + 32;
+  k.tb = K1Geom<T, TX>::NT;
+  static_assert(K1Geom<T, TX>::NT == K2Geom<T, TX, P>::NT, "both kernels use one block size");
   k.ok = true;
   return k;
 }

@@ -301,15 +301,19 @@ __device__ __forceinline__ bool compute_sync_and(bool v) {
   return out != 0;
 }
 
-// The producer loop: rows [mlo, mhi] into NST ring slots. Slot of row n is
-// (n - mlo) % NST; its k-th fill waits for the (k-1)-th release. Returns the
-// last row issued. Bounded: a release that never comes ends the loop.
+// The producer loop: rows [mlo, mhi] into NST ring slots; producer warp w of
+// P handles rows mlo + w, mlo + w + P, ... (a bulk copy blocks its issuing
+// thread for several hundred ns, so several warps issue side by side). Slot
+// of row n is (n - mlo) % NST; its k-th fill waits for the (k-1)-th release.
+// Returns the last row issued. Bounded: a release that never comes ends the
+// loop.
 template <int NST>
 __device__ __forceinline__ int produce_rows(const RowCopy &c, unsigned char *ring, int slot_bytes, uint64_t *full,
                                             uint64_t *empty, int mlo, int mhi, size_t pitch_bytes, int j0,
-                                            bool skip_first, uint64_t timeout_ns, const volatile int *abort) {
+                                            bool skip_first, uint64_t timeout_ns, const volatile int *abort,
+                                            int first, int stride) {
   int last = mlo - 1;
-  for (int n = mlo; n <= mhi; ++n) {
+  for (int n = mlo + first; n <= mhi; n += stride) {
     const int slot = (NST & (NST - 1)) == 0 ? ((n - mlo) & (NST - 1)) : ((n - mlo) % NST), fill = (n - mlo) / NST;
     if (fill > 0) {
       bool ok = true;
@@ -340,21 +344,23 @@ struct K1Geom {
   static constexpr int WT = TX;                      // c_n, a, x / b
   static constexpr int NST = 8;                      // ring slots (a power of two): rows m-3..m live, 4 ahead
   static constexpr int NDN = 4;                      // rows of d' kept (a power of two)
-  static constexpr int NT = TX + 32;                 // compute threads + producer warp
+  static constexpr int NPW = 1;                      // producer warps
+  static constexpr int NT = TX + 32 * NPW;           // compute threads + producer warps
   static constexpr int OFF_S = 0, OFF_D = WS, OFF_E = 2 * WS, OFF_N = 2 * WS + WE, OFF_A = OFF_N + WT,
                        OFF_X = OFF_A + WT, SLOT = OFF_X + WT;
   static constexpr int WDN = TX + 2;                 // d' ring: [i0-1, i0+TX+1)
   static constexpr size_t SMEM = 256 + sizeof(T) * ((size_t)NST * SLOT + NDN * WDN) + 16 * (NT / 32) + 64;
+  static_assert(2 * NST * 8 <= 224 && 3 + NPW <= 8, "barrier / control area of the first 256 bytes");
 };
 
 template <typename T, int TX>
-__global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
+__global__ void __launch_bounds__(TX + 32 * K1Geom<T, TX>::NPW) k_stencil(KParams p) {
   using G = K1Geom<T, TX>;
   constexpr int NT = G::NT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
   uint64_t *empty = full + G::NST;
-  volatile int *ctl = reinterpret_cast<volatile int *>(smem_raw + 224);   // abort, issued, consumed
+  volatile int *ctl = reinterpret_cast<volatile int *>(smem_raw + 224);   // abort, -, consumed, last row per producer
   unsigned char *ring_b = smem_raw + 256;
   const T *ring = reinterpret_cast<const T *>(ring_b);
   T *dn = reinterpret_cast<T *>(ring_b + sizeof(T) * (size_t)G::NST * G::SLOT);
@@ -382,6 +388,7 @@ __global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
   if (tid == 0) {
     for (int s = 0; s < G::NST; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     ctl[0] = 0; ctl[1] = mlo - 1; ctl[2] = mlo - 1;
+    for (int w = 0; w < G::NPW; ++w) ctl[3 + w] = mlo - 1;
     fence_mbar_init();
   }
   __syncthreads();
@@ -389,8 +396,8 @@ __global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
   double acc0 = 0.0, acc1 = 0.0;
   DotAcc<T> dot0, dot1;
   if (tid >= TX) {
-    // ---- producer warp
-    const int lane = tid - TX;
+    // ---- producer warps
+    const int lane = (tid - TX) & 31, pw = (tid - TX) >> 5;
     RowCopy c{nullptr, 0, 0, 0};
     const T *src = (kind == K1_ITER) ? gdp->s : (kind == K1_SPMV) ? gdp->d[0] : gdp->x;
     auto at = [&](const T *plane, int col) { return reinterpret_cast<const char *>(plane + i0 + col); };
@@ -403,10 +410,10 @@ __global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
       case 5: if (kind != K1_SPMV) c = RowCopy{at(kind == K1_ITER ? gdp->x : gdp->b, 0), (uint32_t)(G::OFF_X * sizeof(T)), (uint32_t)(G::WT * sizeof(T)), 2}; break;
       default: break;
     }
-    const bool skip_first = (p.dbg_skip_unit == (int)blockIdx.x) && lane == 0;
+    const bool skip_first = (p.dbg_skip_unit == (int)blockIdx.x) && lane == 0 && pw == 0;
     const int last = produce_rows<G::NST>(c, ring_b, SLOTB, full, empty, mlo, mhi, pitch_b, j0, skip_first,
-                                          p.timeout_ns, ctl);
-    if (lane == 0) ctl[1] = last;
+                                          p.timeout_ns, ctl, pw, G::NPW);
+    if (lane == 0) ctl[3 + pw] = last;
   } else {
     // ---- compute threads
     const T beta = (kind == K1_ITER) ? (T)st->beta : (T)0;
@@ -477,10 +484,12 @@ __global__ void __launch_bounds__(TX + 32) k_stencil(KParams p) {
     acc1 = dot1.total();
   }
   __syncthreads();
-  if (tid == 0 && ctl[2] < ctl[1]) {
+  if (tid == 0 && ctl[0]) {
     // the compute threads gave up: wait (bounded) for the rows still in flight
-    for (int m = ctl[2] + 1; m <= ctl[1]; ++m)
-      mbar_wait_bounded(&full[(m - mlo) & (G::NST - 1)], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
+    for (int w = 0; w < G::NPW; ++w)
+      for (int m = mlo + w; m <= ctl[3 + w]; m += G::NPW)
+        if (m > ctl[2])
+          mbar_wait_bounded(&full[(m - mlo) & (G::NST - 1)], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
   }
   if (kind == K1_SPMV) return;
   if (grid_reduce2<NT>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt1, red, flag)) {
@@ -532,14 +541,16 @@ struct K2Geom {
   // binary32 is bound by HBM, so it keeps more rows in flight.
   static constexpr int NST = sizeof(T) == 8 ? LD + 4 : pow2_at_least(LD + 5);
   __device__ static constexpr int slot(int x) { return (NST & (NST - 1)) == 0 ? (x & (NST - 1)) : (x % NST); }
-  static constexpr int NT = TX + 32;                 // compute threads + producer warp
+  static constexpr int NPW = 1;                      // producer warps
+  static constexpr int NT = TX + 32 * NPW;           // compute threads + producer warps
   static constexpr int OFF_R = 0, OFF_Q = WR, OFF_Z = 2 * WR, OFF_DI = 2 * WR + NZ * WZ, SLOT = OFF_DI + WZ;
   static constexpr size_t SMEM =
       256 + sizeof(T) * ((size_t)NST * SLOT + (size_t)NRN * WRC + (size_t)NTT * WTC) + 16 * (NT / 32) + 64;
+  static_assert(2 * NST * 8 <= 224 && 3 + NPW <= 8, "barrier / control area of the first 256 bytes");
 };
 
 template <typename T, int TX, class P>
-__global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
+__global__ void __launch_bounds__(TX + 32 * K2Geom<T, TX, P>::NPW) k_precond(KParams p) {
   using G = K2Geom<T, TX, P>;
   constexpr int R = P::R, LD = P::LD, NZ = P::NZ, NW = P::NW, NT = G::NT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -574,6 +585,7 @@ __global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
   if (tid == 0) {
     for (int s = 0; s < G::NST; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     ctl[0] = 0; ctl[1] = mlo - 1; ctl[2] = mlo - 1;
+    for (int w = 0; w < G::NPW; ++w) ctl[3 + w] = mlo - 1;
     fence_mbar_init();
   }
   __syncthreads();
@@ -581,18 +593,18 @@ __global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
   double acc0 = 0.0, acc1 = 0.0;
   DotAcc<T> dot0, dot1;
   if (tid >= TX) {
-    // ---- producer warp
-    const int lane = tid - TX;
+    // ---- producer warps
+    const int lane = (tid - TX) & 31, pw = (tid - TX) >> 5;
     auto at = [&](const T *plane, int col) { return reinterpret_cast<const char *>(plane + i0 + col); };
     RowCopy c{nullptr, 0, 0, 0};
     if (lane == 0) c = RowCopy{at(gdp->r[rsel], -G::HR), (uint32_t)(G::OFF_R * sizeof(T)), (uint32_t)(G::WR * sizeof(T)), 0};
     else if (lane == 1) { if (kind == K2_ITER) c = RowCopy{at(gdp->q, -G::HR), (uint32_t)(G::OFF_Q * sizeof(T)), (uint32_t)(G::WR * sizeof(T)), 0}; }
     else if (lane - 2 < NZ) c = RowCopy{at(gdp->z[lane - 2], -G::HZ), (uint32_t)((G::OFF_Z + (lane - 2) * G::WZ) * sizeof(T)), (uint32_t)(G::WZ * sizeof(T)), 3};
     else if (lane - 2 == NZ) c = RowCopy{at(gdp->dinv, -G::HZ), (uint32_t)(G::OFF_DI * sizeof(T)), (uint32_t)(G::WZ * sizeof(T)), 3};
-    const bool skip_first = (p.dbg_skip_unit == (int)blockIdx.x) && lane == 0;
+    const bool skip_first = (p.dbg_skip_unit == (int)blockIdx.x) && lane == 0 && pw == 0;
     const int last = produce_rows<G::NST>(c, ring_b, SLOTB, full, empty, mlo, mhi, pitch_b, j0, skip_first,
-                                          p.timeout_ns, ctl);
-    if (lane == 0) ctl[1] = last;
+                                          p.timeout_ns, ctl, pw, G::NPW);
+    if (lane == 0) ctl[3 + pw] = last;
   } else {
     // ---- compute threads
     const T alpha = (kind == K2_ITER) ? (T)st->alpha : (T)0;
@@ -688,9 +700,11 @@ __global__ void __launch_bounds__(TX + 32) k_precond(KParams p) {
     acc1 = dot1.total();
   }
   __syncthreads();
-  if (tid == 0 && ctl[2] < ctl[1]) {
-    for (int m = ctl[2] + 1; m <= ctl[1]; ++m)
-      mbar_wait_bounded(&full[G::slot(m - mlo)], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
+  if (tid == 0 && ctl[0]) {
+    for (int w = 0; w < G::NPW; ++w)
+      for (int m = mlo + w; m <= ctl[3 + w]; m += G::NPW)
+        if (m > ctl[2])
+          mbar_wait_bounded(&full[G::slot(m - mlo)], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
   }
   if (kind == K2_APPLY) return;
   if (grid_reduce2<NT>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt2, red, flag)) {
