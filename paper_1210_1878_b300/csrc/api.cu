@@ -1,6 +1,8 @@
 // Host side of libpcg: device planes, launch plans, the device-resident PCG
 // loop (a CUDA graph whose conditional WHILE node repeats the two kernels of
 // an iteration until every grid's stopping test has fired), and the C ABI.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,8 +28,13 @@ void set_error(const std::string &m) { g_err = m; }
 template <typename T, int TX, class P>
 static KernelSet make_set() {
   KernelSet k;
-  k.k1 = (const void *)k_stencil<T, TX>;
-  k.k2 = (const void *)k_precond<T, TX, P>;
+  k.k1[K1_ITER] = (const void *)k_stencil<T, TX, K1_ITER>;
+  k.k1[K1_RESID_INIT] = (const void *)k_stencil<T, TX, K1_RESID_INIT>;
+  k.k1[K1_RESID_CHECK] = (const void *)k_stencil<T, TX, K1_RESID_CHECK>;
+  k.k1[K1_SPMV] = (const void *)k_stencil<T, TX, K1_SPMV>;
+  k.k2[K2_ITER] = (const void *)k_precond<T, TX, P, K2_ITER>;
+  k.k2[K2_INIT] = (const void *)k_precond<T, TX, P, K2_INIT>;
+  k.k2[K2_APPLY] = (const void *)k_precond<T, TX, P, K2_APPLY>;
   k.fin = (const void *)k_finalize<T, TX>;
   k.pack = (const void *)k_pack<T, double, TX>;
   k.unpack = (const void *)k_unpack<T, double>;
@@ -35,6 +42,10 @@ static KernelSet make_set() {
   k.smem2 = K2Geom<T, TX, P>::SMEM;
   k.tx = TX;
   k.tb = K1Geom<T, TX>::NT;
+  k.rb1 = K1Geom<T, TX>::RB;
+  k.rb2 = K2Geom<T, TX, P>::RB;
+  k.ws = K1Geom<T, TX>::WS; k.we = K1Geom<T, TX>::WE; k.wt = K1Geom<T, TX>::WT;
+  k.wr = K2Geom<T, TX, P>::WR; k.wz = K2Geom<T, TX, P>::WZ;
   static_assert(K1Geom<T, TX>::NT == K2Geom<T, TX, P>::NT, "both kernels use one block size");
   k.ok = true;
   return k;
@@ -72,18 +83,103 @@ static KernelSet pick(int tx, int pattern, int q) {
 }
 
 static std::mutex g_attr_mu;
-static int prepare_set(const KernelSet &k) {
+static int prepare_set(KernelSet &k) {
   std::lock_guard<std::mutex> lk(g_attr_mu);
-  CK(cudaFuncSetAttribute(k.k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem1));
-  CK(cudaFuncSetAttribute(k.k2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem2));
+  for (const void *f : k.k1) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem1));
+  for (const void *f : k.k2) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem2));
+  int dev = 0, nsm = 0, b1 = 0, b2 = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  b1 = b2 = 1 << 20;
+  for (const void *f : k.k1) {
+    int b = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, k.tb, k.smem1));
+    b1 = std::min(b1, b);
+  }
+  for (const void *f : k.k2) {
+    int b = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, k.tb, k.smem2));
+    b2 = std::min(b2, b);
+  }
+  if (b1 < 1 || b2 < 1) { set_error("kernel does not fit on an SM"); return PCG_ECUDA; }
+  k.ctas1 = b1 * nsm;
+  k.ctas2 = b2 * nsm;
   return PCG_OK;
 }
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+static_assert(sizeof(CUtensorMap) == sizeof(TensorMapBytes), "tensor map size");
 
 }  // namespace pcg
 
 namespace pcg {
 
 static size_t elem_round(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Tensor map of plane idx (all stored columns and rows, row-major with the
+// plane's pitch) whose box is w columns by rb rows.
+template <typename T>
+static int make_tensor_map(TensorMapBytes &out, const DevPlanes<T> &P, int idx, int w, int rb) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) { set_error("cuTensorMapEncodeTiled unavailable"); return PCG_ECUDA; }
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {(cuuint64_t)P.pitch, (cuuint64_t)(P.ny + 2 * GY)};
+  const cuuint64_t strides[1] = {(cuuint64_t)P.pitch * sizeof(T)};
+  const cuuint32_t box[2] = {(cuuint32_t)w, (cuuint32_t)rb};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = enc(&m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                         (void *)P.plane_start(idx), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { set_error("tensor map encoding failed (" + std::to_string((int)r) + ")"); return PCG_ECUDA; }
+  std::memcpy(&out, &m, sizeof(m));
+  return PCG_OK;
+}
+
+template <typename T>
+static int upload_tensor_maps(DevPlanes<T> &P) {
+  const KernelSet &k = P.ks;
+  if (k.rb1 == 1 && k.rb2 == 1) return PCG_OK;
+  std::vector<TensorMapBytes> tm(TM_COUNT);
+  std::memset(tm.data(), 0, sizeof(TensorMapBytes) * TM_COUNT);
+  int rc;
+  struct Spec { int slot, plane, w, rb; };
+  std::vector<Spec> specs;
+  if (k.rb1 > 1) {
+    specs.insert(specs.end(), {{TM_WS_S, P.vec(1), k.ws, k.rb1}, {TM_WS_D0, P.vec(5), k.ws, k.rb1},
+                               {TM_WS_D1, P.vec(6), k.ws, k.rb1}, {TM_WS_X, P.vec(0), k.ws, k.rb1},
+                               {TM_WT_CN, PL_CN, k.wt, k.rb1}, {TM_WT_A, PL_A, k.wt, k.rb1},
+                               {TM_WT_X, P.vec(0), k.wt, k.rb1}, {TM_WT_B, P.vec(7), k.wt, k.rb1},
+                               {TM_WE_CE, PL_CE, k.we, k.rb1}});
+  }
+  if (k.rb2 > 1) {
+    specs.insert(specs.end(), {{TM_WR_R0, P.vec(3), k.wr, k.rb2}, {TM_WR_R1, P.vec(4), k.wr, k.rb2},
+                               {TM_WR_Q, P.vec(2), k.wr, k.rb2}, {TM_WZ_DI, PL_DINV, k.wz, k.rb2}});
+    for (int z = 0; z < P.nz; ++z) specs.push_back({TM_WZ_Z0 + z, PL_Z0 + z, k.wz, k.rb2});
+  }
+  for (const Spec &sp : specs)
+    if ((rc = make_tensor_map<T>(tm[sp.slot], P, sp.plane, sp.w, sp.rb))) return rc;
+  CK(cudaMalloc(&P.tm, sizeof(TensorMapBytes) * TM_COUNT));
+  CK(cudaMemcpy(P.tm, tm.data(), sizeof(TensorMapBytes) * TM_COUNT, cudaMemcpyHostToDevice));
+  P.bytes += sizeof(TensorMapBytes) * TM_COUNT;
+  return PCG_OK;
+}
 
 template <typename T>
 static int upload_planes(pcg_handle *h, DevPlanes<T> &P, cudaStream_t s) {
@@ -167,6 +263,8 @@ static int upload_planes(pcg_handle *h, DevPlanes<T> &P, cudaStream_t s) {
   gd.d[0] = P.plane(P.vec(5)); gd.d[1] = P.plane(P.vec(6));
   gd.b = P.plane(P.vec(7));
   gd.partial = P.partial; gd.st = P.st;
+  if ((rc = upload_tensor_maps(P))) return rc;
+  gd.tm = P.tm;
   CK(cudaMemcpy(P.gd_dev, &gd, sizeof(gd), cudaMemcpyHostToDevice));
   if (P.n_units > 0) CK(cudaMemcpy(P.units_dev, P.units.data(), sizeof(Unit) * P.n_units, cudaMemcpyHostToDevice));
   return PCG_OK;
@@ -202,6 +300,14 @@ static int launch(const void *f, int grid, int block, size_t smem, KParams p, cu
   return PCG_OK;
 }
 
+// Kernel 1 (which = 1) or 2 over n_units units, persistent CTAs.
+static int launch_k(const KernelSet &ks, int which, int n_units, KParams p, cudaStream_t s) {
+  p.n_units = n_units;
+  if (p.kind < 0 || p.kind >= (which == 1 ? 4 : 3)) { set_error("invalid launch kind"); return PCG_EINVAL; }
+  return launch(which == 1 ? ks.k1[p.kind] : ks.k2[p.kind], persistent_grid(ks, which, n_units), ks.tb,
+                which == 1 ? ks.smem1 : ks.smem2, p, s);
+}
+
 static int build_loop_graph(LoopPlan &L) {
   if (getenv("PCG_LOOP_CHUNKED")) return PCG_ECUDA;
   cudaGraph_t g = nullptr;
@@ -231,10 +337,11 @@ static int build_loop_graph(LoopPlan &L) {
       const int guard = (pass == 1 && !guarded) ? 1 : 0;   // the first preconditioner launch of the body
       guarded = guarded || guard;
       params.push_back(kparams(L, G, pass == 0 ? (int)K1_ITER : (int)K2_ITER, 1, guard));
+      params.back().n_units = G.n_units;
       void *args[] = {&params.back()};
       cudaKernelNodeParams kp{};
-      kp.func = const_cast<void *>(pass == 0 ? G.ks.k1 : G.ks.k2);
-      kp.gridDim = dim3(G.n_units);
+      kp.func = const_cast<void *>(pass == 0 ? G.ks.k1[K1_ITER] : G.ks.k2[K2_ITER]);
+      kp.gridDim = dim3(persistent_grid(G.ks, pass == 0 ? 1 : 2, G.n_units));
       kp.blockDim = dim3(G.ks.tb);
       kp.sharedMemBytes = (unsigned)(pass == 0 ? G.ks.smem1 : G.ks.smem2);
       kp.kernelParams = args;
@@ -292,8 +399,8 @@ int members_loop(LoopPlan &L, LaunchState *ls_host, int max_launches, cudaStream
           if (G.n_units <= 0) continue;
           const int guard = (pass == 1 && !guarded) ? 1 : 0;
           guarded = guarded || guard;
-          int rc = launch(pass == 0 ? G.ks.k1 : G.ks.k2, G.n_units, G.ks.tb, pass == 0 ? G.ks.smem1 : G.ks.smem2,
-                          kparams(L, G, pass == 0 ? (int)K1_ITER : (int)K2_ITER, 0, guard), s);
+          int rc = launch_k(G.ks, pass == 0 ? 1 : 2, G.n_units,
+                            kparams(L, G, pass == 0 ? (int)K1_ITER : (int)K2_ITER, 0, guard), s);
           if (rc) return rc;
         }
     }
@@ -368,7 +475,8 @@ static int plan_build_t(LoopPlan &L, pcg_handle *const *hs, int n, bool with_gra
   for (int i = 0; i < n; ++i) {
     bool placed = false;
     for (auto &g : groups)
-      if ((hs[g[0]]->*planes).ks.k2 == (hs[i]->*planes).ks.k2 && (hs[g[0]]->*planes).ks.k1 == (hs[i]->*planes).ks.k1) {
+      if ((hs[g[0]]->*planes).ks.k2[0] == (hs[i]->*planes).ks.k2[0] &&
+          (hs[g[0]]->*planes).ks.k1[0] == (hs[i]->*planes).ks.k1[0]) {
         g.push_back(i); placed = true; break;
       }
     if (!placed) groups.push_back({i});
@@ -419,7 +527,6 @@ int ensure_f32(pcg_handle *h, cudaStream_t s) {
     cudaGetLastError(); set_error("pinned allocation failed"); return PCG_ENOMEM;
   }
   h->bytes += h->p32.bytes;
-  pcg_handle *hs[1] = {h};
   auto L = std::make_unique<LoopPlan>();
   L->ls = h->ls;
   PlanGroup g;
@@ -430,7 +537,6 @@ int ensure_f32(pcg_handle *h, cudaStream_t s) {
   L->groups.push_back(g);
   if (build_loop_graph(*L) != PCG_OK) L->graph_ok = false;
   g_err.clear();
-  (void)hs;
   h->plan32 = std::move(L);
   return PCG_OK;
 }
@@ -474,9 +580,9 @@ int member_load(Member &m, const pcg_opts &o, bool pack_x0, cudaStream_t s) {
 int members_init(LoopPlan &L, cudaStream_t s) {
   int rc;
   for (auto &G : L.groups)
-    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tb, G.ks.smem1, kparams(L, G, K1_RESID_INIT, 0, 0), s))) return rc;
+    if ((rc = launch_k(G.ks, 1, G.n_units, kparams(L, G, K1_RESID_INIT, 0, 0), s))) return rc;
   for (auto &G : L.groups)
-    if ((rc = launch(G.ks.k2, G.n_units, G.ks.tb, G.ks.smem2, kparams(L, G, K2_INIT, 0, 0), s))) return rc;
+    if ((rc = launch_k(G.ks, 2, G.n_units, kparams(L, G, K2_INIT, 0, 0), s))) return rc;
   return PCG_OK;
 }
 
@@ -485,7 +591,7 @@ int members_close(LoopPlan &L, cudaStream_t s) {
   for (auto &G : L.groups)
     if ((rc = launch(G.ks.fin, G.n_units, G.ks.tx, 0, kparams(L, G, 0, 0, 0), s))) return rc;
   for (auto &G : L.groups)
-    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tb, G.ks.smem1, kparams(L, G, K1_RESID_CHECK, 0, 0), s))) return rc;
+    if ((rc = launch_k(G.ks, 1, G.n_units, kparams(L, G, K1_RESID_CHECK, 0, 0), s))) return rc;
   return PCG_OK;
 }
 
@@ -669,7 +775,7 @@ int solve_members_mixed(LoopPlan &L64, LoopPlan &L32, LaunchState *ls_host, std:
     // binary64 residual of every unfinished grid
     if ((rc = members_arm(L64, ls_host, remaining, 1, s))) return rc;
     for (auto &G : L64.groups)
-      if ((rc = launch(G.ks.k1, G.n_units, G.ks.tb, G.ks.smem1, kparams(L64, G, K1_RESID_INIT, 0, 0), s))) return rc;
+      if ((rc = launch_k(G.ks, 1, G.n_units, kparams(L64, G, K1_RESID_INIT, 0, 0), s))) return rc;
     for (auto &m : M) CK(cudaMemcpyAsync(m.st_host, m.h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     int inner = 0;
@@ -721,8 +827,8 @@ void mixed_stats(Member &m) {
 int single_launch(pcg_handle *h, bool f32, int which, int kind, cudaStream_t s) {
   LoopPlan &L = f32 ? *h->plan32 : *h->plan64;
   const PlanGroup &G = L.groups[0];
-  if (which == 1) return launch(G.ks.k1, G.n_units, G.ks.tb, G.ks.smem1, kparams(L, G, kind, 0, 0), s);
-  if (which == 2) return launch(G.ks.k2, G.n_units, G.ks.tb, G.ks.smem2, kparams(L, G, kind, 0, 0), s);
+  if (which == 1) return launch_k(G.ks, 1, G.n_units, kparams(L, G, kind, 0, 0), s);
+  if (which == 2) return launch_k(G.ks, 2, G.n_units, kparams(L, G, kind, 0, 0), s);
   return launch(G.ks.fin, G.n_units, G.ks.tx, 0, kparams(L, G, 0, 0, 0), s);
 }
 
@@ -933,7 +1039,7 @@ int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream) {
   KParams p{};
   p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K1_SPMV; p.dbg_skip_unit = -1;
   p.timeout_ns = default_timeout_ns();
-  if ((rc = launch(P.ks.k1, P.n_units, P.ks.tb, P.ks.smem1, p, s))) return rc;
+  if ((rc = launch_k(P.ks, 1, P.n_units, p, s))) return rc;
   if ((rc = unpack_user(h, q, 2, s))) return rc;
   CK(cudaStreamSynchronize(s));
   return PCG_OK;
@@ -948,7 +1054,7 @@ int pcg_precond_apply(pcg_handle *h, const double *r, double *sv, void *cuda_str
   KParams p{};
   p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K2_APPLY; p.dbg_skip_unit = -1;
   p.timeout_ns = default_timeout_ns();
-  if ((rc = launch(P.ks.k2, P.n_units, P.ks.tb, P.ks.smem2, p, s))) return rc;
+  if ((rc = launch_k(P.ks, 2, P.n_units, p, s))) return rc;
   if ((rc = unpack_user(h, sv, 1, s))) return rc;
   CK(cudaStreamSynchronize(s));
   return PCG_OK;
@@ -980,7 +1086,7 @@ int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, int32_t p
     // b64 -> r64 plane 0 by a residual pass with x = 0, then to binary32
     if ((rc = members_arm(*L, h->ls_host, 1, 1, s))) return rc;
     const PlanGroup &G64 = L->groups[0];
-    if ((rc = launch(G64.ks.k1, G64.n_units, G64.ks.tb, G64.ks.smem1, kparams(*L, G64, K1_RESID_INIT, 0, 0), s))) return rc;
+    if ((rc = launch_k(G64.ks, 1, G64.n_units, kparams(*L, G64, K1_RESID_INIT, 0, 0), s))) return rc;
     double sc = 1.0;
     void *args[] = {(void *)&g64, (void *)&g32, (void *)&un, &sc};
     const void *f = h->tx == 128 ? (const void *)k_residual_to_f32<128> : (const void *)k_residual_to_f32<64>;
@@ -1003,10 +1109,10 @@ int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, int32_t p
   for (auto &e : ev) CK(cudaEventCreate(&e));
   for (int it = 0; it < iters; ++it) {
     CK(cudaEventRecord(ev[4 * it], s));
-    if ((rc = launch(G.ks.k1, G.n_units, G.ks.tb, G.ks.smem1, kparams(*L, G, K1_ITER, 0, 0), s))) return rc;
+    if ((rc = launch_k(G.ks, 1, G.n_units, kparams(*L, G, K1_ITER, 0, 0), s))) return rc;
     CK(cudaEventRecord(ev[4 * it + 1], s));
     CK(cudaEventRecord(ev[4 * it + 2], s));
-    if ((rc = launch(G.ks.k2, G.n_units, G.ks.tb, G.ks.smem2, kparams(*L, G, K2_ITER, 0, 0), s))) return rc;
+    if ((rc = launch_k(G.ks, 2, G.n_units, kparams(*L, G, K2_ITER, 0, 0), s))) return rc;
     CK(cudaEventRecord(ev[4 * it + 3], s));
   }
   CK(cudaStreamSynchronize(s));
@@ -1074,7 +1180,7 @@ int pcg_debug_wait_timeout(pcg_handle *h, int32_t unit, double timeout_ms, void 
   p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K2_INIT;
   p.dbg_skip_unit = unit;
   p.timeout_ns = (uint64_t)(timeout_ms * 1e6);
-  int rc = launch(P.ks.k2, P.n_units, P.ks.tb, P.ks.smem2, p, s);
+  int rc = launch_k(P.ks, 2, P.n_units, p, s);
   if (rc) return rc;
   CK(cudaMemcpyAsync(h->st_host, P.st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));

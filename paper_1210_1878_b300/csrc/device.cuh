@@ -10,11 +10,12 @@
 // needs a mask: it stays zero through every operation.
 //
 // Work units. A grid is cut into strips TX columns wide and TY rows tall; only
-// strips holding a wet cell become units. One CTA of TX threads handles one
-// unit, thread t owning column i0 + t. It marches north one row at a time; one
-// elected thread streams each input row of every field into a ring of
-// shared-memory slots with bulk asynchronous copies (cp.async.bulk, completion
-// counted on an mbarrier per slot), NST rows ahead. Values needed from
+// strips holding a wet cell become units. A persistent CTA of TX compute
+// threads (plus a producer warp) handles a unit at a time, thread t owning
+// column i0 + t. It marches north one row at a time while the producer warp
+// streams the input fields, several rows per copy, into a ring of
+// shared-memory slots (tensor or bulk asynchronous copies, completion counted
+// on an mbarrier per slot), running on into the CTA's next unit. Values needed from
 // neighbouring rows (the stencil's north/south points, the rows Z^T pulls from
 // and the rows Z pushes to) are computed once per row into small shared rings,
 // so every point's floating-point work is done once; only the few halo columns
@@ -61,6 +62,23 @@ struct LaunchState {
   int32_t cond_cleared;    // the loop condition has been cleared in this launch
 };
 
+// A CUtensorMap as the kernels see it: 128 opaque bytes, 64-byte aligned.
+struct alignas(64) TensorMapBytes {
+  unsigned long long w[16];
+};
+
+// Tensor maps of a grid (RB > 1 streaming), one per plane and box width:
+// WS = TX + 2H, WT = TX, WE = TX + H of the stencil kernel; WR, WZ of the
+// preconditioner kernel.
+enum {
+  TM_WS_S = 0, TM_WS_D0, TM_WS_D1, TM_WS_X,
+  TM_WT_CN, TM_WT_A, TM_WT_X, TM_WT_B,
+  TM_WE_CE,
+  TM_WR_R0, TM_WR_R1, TM_WR_Q,
+  TM_WZ_DI, TM_WZ_Z0,
+  TM_COUNT = TM_WZ_Z0 + 8
+};
+
 template <typename T>
 struct GridDev {
   int32_t nx, ny, pitch, ty;
@@ -73,6 +91,7 @@ struct GridDev {
   const T *b;
   double *partial;         // [n_units][2]
   SolveState *st;
+  const TensorMapBytes *tm;   // [TM_COUNT] or null (one row per copy)
 };
 
 struct Unit {              // one strip of one grid
@@ -90,6 +109,8 @@ struct KParams {
   int32_t guard;           // 1 for the first stencil launch of the loop body
   int32_t dbg_skip_unit;   // test hook: unit whose first row copy is never issued (-1: none)
   uint64_t timeout_ns;     // bound on every mbarrier wait
+  int32_t n_units;         // units in the list; CTAs stride over them (persistent)
+  int32_t pad;
 };
 
 }  // namespace pcg

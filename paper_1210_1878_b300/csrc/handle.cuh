@@ -22,12 +22,23 @@ namespace pcg {
   } while (0)
 
 struct KernelSet {
-  const void *k1 = nullptr, *k2 = nullptr, *fin = nullptr, *pack = nullptr, *unpack = nullptr;
+  const void *k1[4] = {}, *k2[3] = {};      // per launch kind (K1_*, K2_*)
+  const void *fin = nullptr, *pack = nullptr, *unpack = nullptr;
   size_t smem1 = 0, smem2 = 0;
   int tx = 0;        // strip width: threads of the small kernels
   int tb = 0;        // threads of the stencil and preconditioner kernels (tx + a producer warp)
+  int rb1 = 1, rb2 = 1;                       // rows per streamed group of the two kernels
+  int ws = 0, we = 0, wt = 0, wr = 0, wz = 0; // box widths of the streamed fields
+  int ctas1 = 0, ctas2 = 0;                   // resident CTAs on the device (persistent grid size)
   bool ok = false;
 };
+
+// CTAs of a launch of kernel 1 or 2 over n units: one per unit up to the
+// number resident at once; the CTAs then stride over the units.
+inline int persistent_grid(const KernelSet &k, int which, int n_units) {
+  const int cap = which == 1 ? k.ctas1 : k.ctas2;
+  return n_units < cap ? n_units : cap;
+}
 
 enum { PL_CE = 0, PL_CN, PL_A, PL_DINV, PL_Z0 };
 
@@ -37,6 +48,7 @@ struct DevPlanes {
   size_t plane_elems = 0;
   T *mem = nullptr;
   T *zwrap = nullptr;
+  TensorMapBytes *tm = nullptr;    // device [TM_COUNT], when a kernel streams several rows per copy
   double *partial = nullptr;
   SolveState *st = nullptr;
   GridDev<T> gd{};
@@ -53,7 +65,9 @@ struct DevPlanes {
 
   void release() {
     cudaFree(mem); cudaFree(zwrap); cudaFree(partial); cudaFree(st); cudaFree(gd_dev); cudaFree(units_dev);
+    cudaFree(tm);
     mem = nullptr; zwrap = nullptr; partial = nullptr; st = nullptr; gd_dev = nullptr; units_dev = nullptr;
+    tm = nullptr;
   }
 };
 

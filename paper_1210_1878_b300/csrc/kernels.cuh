@@ -105,6 +105,11 @@ struct Pat<PCG_PAT_BAND_T, Q> {
 };
 
 __host__ __device__ constexpr int round_up_c(int v, int a) { return (v + a - 1) / a * a; }
+// Group slots of a ring: as many as fit in `budget` bytes, at least live + 1
+// and at most 8.
+__host__ __device__ constexpr int ring_groups(int budget, int group, int live) {
+  return budget / group < live + 1 ? live + 1 : (budget / group > 8 ? 8 : budget / group);
+}
 __host__ __device__ constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : 2 * pow2_at_least((v + 1) / 2); }
 
 // Exact widening of binary32 to binary64 with integer operations only (IEEE
@@ -161,6 +166,17 @@ __device__ __forceinline__ void store_dup(T *row, int col, int nx, T v) {
   if (col < GHOST)
     for (int c = col + nx; c < nx + GHOST; c += nx) row[c] = v;
   if (col >= nx - GHOST)
+    for (int c = col - nx; c >= -GHOST; c -= nx) row[c] = v;
+}
+
+// As store_dup, for a thread whose column is fixed: lo = (col < GHOST) and
+// hi = (col >= nx - GHOST) are computed once.
+template <typename T>
+__device__ __forceinline__ void store_col(T *row, int col, int nx, T v, bool lo, bool hi) {
+  row[col] = v;
+  if (lo)
+    for (int c = col + nx; c < nx + GHOST; c += nx) row[c] = v;
+  if (hi)
     for (int c = col - nx; c >= -GHOST; c -= nx) row[c] = v;
 }
 
@@ -246,42 +262,58 @@ __device__ __forceinline__ void loop_guard(LaunchState *ls, const KParams &p) {
 
 __device__ __forceinline__ void flag_timeout(SolveState *st) { atomicCAS(&st->status, PCG_OK, PCG_ETIMEOUT); }
 
-// ------------------------------------------------------------ row streaming
-// A CTA is TX compute threads plus one producer warp. The producer streams
-// rows: lane a owns field a of a row (source plane, place in a ring slot,
-// size) and issues its bulk copy (cp.async.bulk) into the slot; lane 0 first
-// arms the slot's "full" mbarrier with the row's byte count. A bulk copy
-// occupies its issuing thread for several hundred ns on this GPU, so the
-// producer runs ahead on its own and the compute threads never wait for an
-// issue, only for data. When the compute threads are done with a row, one of
-// them arrives on the slot's "empty" mbarrier; the producer waits for that
-// before it refills the slot.
-struct RowCopy {
-  const char *src;             // element (i0 - halo, row 0) of the plane, as bytes
-  uint32_t dst;                // byte offset inside a ring slot
-  uint32_t bytes;
-  int when;                    // 0: every streamed row; 1: rows < mhi; 2: rows in [j0, mhi); 3: rows >= j0
+// ------------------------------------------------------------ row-group streaming
+// A CTA is TX compute threads plus one producer warp, and it is persistent:
+// it takes the units blockIdx.x, blockIdx.x + gridDim.x, ... of the launch's
+// list. The producer streams the input fields of its units, unit after unit
+// without a pause, in groups of RB consecutive rows into a ring of NSG group
+// slots. Lane f of the producer owns field f and issues one copy per group: a
+// 2D tensor tile of RB rows (cp.async.bulk.tensor) when RB > 1, a 1D bulk copy
+// of the row (cp.async.bulk) when RB = 1. Lane 0 first arms the slot's "full"
+// mbarrier with the group's byte count. The compute threads wait on "full"
+// when they reach the first row of a group; once no later step reads the
+// group's rows, one of them arrives on the slot's "empty" mbarrier, which the
+// producer waits on before it refills the slot. Copies are the unit of cost
+// here (each occupies its issuing thread for a few hundred ns on this GPU), so
+// several rows per copy is what lets a few CTAs per SM keep HBM busy.
+
+// control words at the start of shared memory (after the barriers)
+enum { CTL_ABORT = 0, CTL_ARMED = 1, CTL_SEEN = 2, CTL_FLAG = 3 };
+
+struct FieldCopy {
+  const char *src;      // RB = 1: element (first box column, row 0) of the plane, as bytes
+  const void *tmap;     // RB > 1: tensor map of the plane with this field's box
+  int32_t x;            // RB > 1: first box column, counted from the plane's first stored column
+  uint32_t dst;         // byte offset of the field in a group slot
+  uint32_t bytes;       // bytes of the field in one group
 };
 
-__device__ __forceinline__ bool row_wanted(int when, int m, int j0, int mhi) {
-  switch (when) {
-    case 1: return m < mhi;
-    case 2: return m >= j0 && m < mhi;
-    case 3: return m >= j0;
-    default: return true;
-  }
+// 2D tensor tile (box of the map) at column x, row y of the map into shared
+// memory (128-byte aligned); completion counted on bar. x * sizeof(element)
+// is a multiple of 16 by construction of every caller.
+__device__ __forceinline__ void tma_2d_g2s(void *dst, const void *tmap, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_addr(bar))
+      : "memory");
 }
 
-// Issue row m into its slot (producer warp, all lanes).
-__device__ __forceinline__ void issue_row(const RowCopy &c, unsigned char *slot_base, uint64_t *full, int m,
-                                          size_t pitch_bytes, int j0, int mhi, bool skip) {
-  const bool want = c.src && row_wanted(c.when, m, j0, mhi);
-  const uint32_t total = __reduce_add_sync(0xffffffffu, want ? c.bytes : 0u);
-  if ((threadIdx.x & 31) == 0) mbar_arrive_expect_tx(full, total);
-  __syncwarp();
-  if (want && !skip) {
-    fence_proxy_async();
-    bulk_g2s(slot_base + c.dst, c.src + (ptrdiff_t)m * (ptrdiff_t)pitch_bytes, c.bytes, full);
+// The tensor maps live in global memory, written by the host: acquire them
+// for the tensor-map proxy before the first copy that uses them.
+__device__ __forceinline__ void tensormap_acquire(const void *tmap) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
+}
+
+// Wait for a phase of an mbarrier, giving up after timeout_ns or as soon as
+// the CTA's abort word is set.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, uint64_t timeout_ns,
+                                                   const volatile int *abort) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63u) == 0 && (*abort || global_ns() - t0 > timeout_ns)) return false;
   }
 }
 
@@ -289,42 +321,138 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Barrier of the NT compute threads only (named barrier 1), with an AND vote.
-template <int NT>
+// Barrier of the NC compute threads only (named barrier 1), with an AND vote.
+template <int NC>
 __device__ __forceinline__ bool compute_sync_and(bool v) {
   uint32_t out;
   asm volatile(
       "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n barrier.cta.red.and.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(out)
-      : "r"((uint32_t)v), "r"(NT)
+      : "r"((uint32_t)v), "r"(NC)
       : "memory");
   return out != 0;
 }
+template <int NC>
+__device__ __forceinline__ void compute_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory");
+}
 
-// The producer loop: rows [mlo, mhi] into NST ring slots; producer warp w of
-// P handles rows mlo + w, mlo + w + P, ... (a bulk copy blocks its issuing
-// thread for several hundred ns, so several warps issue side by side). Slot
-// of row n is (n - mlo) % NST; its k-th fill waits for the (k-1)-th release.
-// Returns the last row issued. Bounded: a release that never comes ends the
-// loop.
-template <int NST>
-__device__ __forceinline__ int produce_rows(const RowCopy &c, unsigned char *ring, int slot_bytes, uint64_t *full,
-                                            uint64_t *empty, int mlo, int mhi, size_t pitch_bytes, int j0,
-                                            bool skip_first, uint64_t timeout_ns, const volatile int *abort,
-                                            int first, int stride) {
-  int last = mlo - 1;
-  for (int n = mlo + first; n <= mhi; n += stride) {
-    const int slot = (NST & (NST - 1)) == 0 ? ((n - mlo) & (NST - 1)) : ((n - mlo) % NST), fill = (n - mlo) / NST;
+// Stream the ng groups of one unit (first rows mlo, mlo + RB, ...). gq is the
+// CTA's running group count; new_grid: the unit's grid differs from the
+// previous unit's (its tensor maps are acquired). Returns false once the CTA
+// is aborting.
+template <int NSG, int RB>
+__device__ __forceinline__ bool produce_unit(const FieldCopy &c, bool has, unsigned char *ring, int group_bytes,
+                                             uint64_t *full, uint64_t *empty, int mlo, int ng, uint32_t &gq,
+                                             size_t pitch_b, bool skip_first, bool new_grid, uint64_t timeout_ns,
+                                             volatile int *ctl) {
+  const int lane = threadIdx.x & 31;
+  if constexpr (RB > 1)
+    if (has && new_grid) tensormap_acquire(c.tmap);
+  const uint32_t total = __reduce_add_sync(0xffffffffu, has ? c.bytes : 0u);
+  for (int q = 0; q < ng; ++q, ++gq) {
+    const uint32_t slot = gq % NSG, fill = gq / NSG;
     if (fill > 0) {
       bool ok = true;
-      if ((threadIdx.x & 31) == 0) ok = mbar_wait_bounded(&empty[slot], (uint32_t)((fill - 1) & 1), timeout_ns);
-      ok = __shfl_sync(0xffffffffu, ok, 0) && !*abort;
-      if (!ok) break;
+      if (lane == 0) ok = mbar_wait_or_abort(&empty[slot], (fill - 1) & 1u, timeout_ns, &ctl[CTL_ABORT]);
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
+        if (lane == 0) ctl[CTL_ABORT] = 1;
+        return false;
+      }
     }
-    issue_row(c, ring + (size_t)slot * slot_bytes, &full[slot], n, pitch_bytes, j0, mhi, skip_first && n == mlo);
-    last = n;
+    if (lane == 0) mbar_arrive_expect_tx(&full[slot], total);
+    __syncwarp();
+    if (has && !(skip_first && q == 0)) {
+      fence_proxy_async();
+      unsigned char *dst = ring + (size_t)slot * group_bytes + c.dst;
+      const int m0 = mlo + q * RB;
+      if constexpr (RB == 1) bulk_g2s(dst, c.src + (ptrdiff_t)m0 * (ptrdiff_t)pitch_b, c.bytes, &full[slot]);
+      else tma_2d_g2s(dst, c.tmap, c.x, m0 + GY, &full[slot]);
+    }
   }
-  return last;
+  return true;
+}
+
+// Shared-memory geometry common to both kernels: barriers and control words
+// in the first 256 bytes of a 128-byte aligned base, then the group ring.
+template <int NSG>
+struct RingCtl {
+  static_assert(NSG <= 12, "barrier area");
+  uint64_t *full, *empty;
+  volatile int *ctl;
+  unsigned char *ring;
+  __device__ __forceinline__ explicit RingCtl(unsigned char *base) {
+    full = reinterpret_cast<uint64_t *>(base);
+    empty = full + NSG;
+    ctl = reinterpret_cast<volatile int *>(base + 192);
+    ring = base + 256;
+  }
+};
+
+__device__ __forceinline__ unsigned char *align128(unsigned char *p) {
+  const uint32_t a = smem_addr(p);
+  return p + ((128u - (a & 127u)) & 127u);
+}
+
+// Sum (a, b) over the NC compute threads; the totals end in thread 0.
+template <int NC>
+__device__ __forceinline__ void compute_sum2(double &a, double &b, double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  compute_sync<NC>();
+  if (lane == 0) { red[2 * w] = a; red[2 * w + 1] = b; }
+  compute_sync<NC>();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+#pragma unroll
+    for (int i = 0; i < NC / 32; ++i) { sa += red[2 * i]; sb += red[2 * i + 1]; }
+    a = sa; b = sb;
+  }
+}
+
+// Write one unit's partials; return true (in every compute thread) if it was
+// the last unit of its grid to arrive, in which case (sa, sb) hold the grid's
+// totals in thread 0, summed in unit order.
+template <int NC>
+__device__ __forceinline__ bool unit_reduce2(double &sa, double &sb, double *partial, int u, int n_units,
+                                             uint32_t *counter, double *red, volatile int *flag) {
+  compute_sum2<NC>(sa, sb, red);
+  if (threadIdx.x == 0) {
+    partial[2 * u] = sa;
+    partial[2 * u + 1] = sb;
+    __threadfence();
+    const uint32_t prev = atomicAdd(counter, 1u);
+    *flag = (prev == (uint32_t)(n_units - 1));
+  }
+  compute_sync<NC>();
+  if (!*flag) return false;
+  __threadfence();
+  double a = 0.0, b = 0.0;
+  for (int t = threadIdx.x; t < n_units; t += NC) {
+    a += __ldcg(partial + 2 * t);
+    b += __ldcg(partial + 2 * t + 1);
+  }
+  compute_sum2<NC>(a, b, red);
+  if (threadIdx.x == 0) {
+    sa = a; sb = b;
+    atomicExch(counter, 0u);
+  }
+  return true;
+}
+
+// Drain at the end of a CTA that aborted: wait (bounded) for the groups armed
+// but never seen by the compute threads, so no copy lands after exit.
+template <int NSG>
+__device__ __forceinline__ void drain_groups(const RingCtl<NSG> &rc, uint64_t timeout_ns) {
+  if (threadIdx.x == 0 && rc.ctl[CTL_ABORT]) {
+    const uint32_t armed = (uint32_t)rc.ctl[CTL_ARMED];
+    for (uint32_t g = (uint32_t)rc.ctl[CTL_SEEN]; g < armed; ++g)
+      mbar_wait_bounded(&rc.full[g % NSG], (g / NSG) & 1u, timeout_ns);
+  }
 }
 
 // ------------------------------------------------------------ kernel 1
@@ -342,177 +470,327 @@ struct K1Geom {
   static constexpr int WS = TX + 2 * H;              // s, d_old / x / v: [i0-H, i0+TX+H)
   static constexpr int WE = TX + H;                  // c_e: [i0-H, i0+TX)
   static constexpr int WT = TX;                      // c_n, a, x / b
-  static constexpr int NST = 8;                      // ring slots (a power of two): rows m-3..m live, 4 ahead
-  static constexpr int NDN = 4;                      // rows of d' kept (a power of two)
-  static constexpr int NPW = 1;                      // producer warps
-  static constexpr int NT = TX + 32 * NPW;           // compute threads + producer warps
-  static constexpr int OFF_S = 0, OFF_D = WS, OFF_E = 2 * WS, OFF_N = 2 * WS + WE, OFF_A = OFF_N + WT,
-                       OFF_X = OFF_A + WT, SLOT = OFF_X + WT;
   static constexpr int WDN = TX + 2;                 // d' ring: [i0-1, i0+TX+1)
-  static constexpr size_t SMEM = 256 + sizeof(T) * ((size_t)NST * SLOT + NDN * WDN) + 16 * (NT / 32) + 64;
-  static_assert(2 * NST * 8 <= 224 && 3 + NPW <= 8, "barrier / control area of the first 256 bytes");
+  static constexpr int NDN = 4;                      // rows of d' kept (a power of two)
+  static constexpr int RB = sizeof(T) == 4 ? 4 : 1;  // rows per group
+  static constexpr int FA = RB > 1 ? 128 : 16;       // alignment of a field in a group
+  __host__ __device__ static constexpr int fb(int w) { return round_up_c(RB * w * (int)sizeof(T), FA); }
+  static constexpr int OFF_S = 0, OFF_D = OFF_S + fb(WS), OFF_N = OFF_D + fb(WS), OFF_E = OFF_N + fb(WT),
+                       OFF_A = OFF_E + fb(WE), OFF_X = OFF_A + fb(WT), GROUP = OFF_X + fb(WT);   // bytes
+  // group slots: the groups a step reads (rows m-3..m) plus at least one in
+  // flight. The binary32 kernel is bound by its compute warps, so its ring is
+  // kept small (about 40 KB) for CTAs per SM.
+  static constexpr int LIVE = (3 + RB - 1) / RB + 1;
+  static constexpr int NSG = RB == 1 ? 8 : ring_groups(40000, GROUP, LIVE);
+  static constexpr int NT = TX + 32;                 // compute threads + the producer warp
+  static constexpr size_t SMEM = 128 + 256 + (size_t)NSG * GROUP + sizeof(T) * (size_t)NDN * WDN + 16 * (NT / 32) + 64;
 };
 
-template <typename T, int TX>
-__global__ void __launch_bounds__(TX + 32 * K1Geom<T, TX>::NPW) k_stencil(KParams p) {
+// Compile-time row bookkeeping of the unrolled step loops: floor division
+// and non-negative remainder.
+__host__ __device__ constexpr int fdiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+__host__ __device__ constexpr int pmod(int a, int b) { return ((a % b) + b) % b; }
+
+// A compute thread's column store with its periodic copies. When the grid is
+// at least GHOST wide a column has at most two copies, col + nx (if col <
+// GHOST) and col - nx (if col >= nx - GHOST): predicated stores. Narrower
+// grids take the general loop.
+template <typename T>
+struct ColStore {
+  int col, nx, da, db;
+  bool pa, pb, tiny;
+  __device__ __forceinline__ void init(int c, int n) {
+    col = c; nx = n;
+    pa = c < GHOST; da = c + n;
+    pb = c >= n - GHOST; db = c - n;
+    tiny = n < GHOST;
+  }
+  __device__ __forceinline__ void put(T *row, T v) const {
+    row[col] = v;
+    if (tiny) {
+      store_col(row, col, nx, v, pa, pb);
+    } else {
+      if (pa) row[da] = v;
+      if (pb) row[db] = v;
+    }
+  }
+};
+
+// One unit of k_stencil on the compute side. The step loop is unrolled by 8
+// (a multiple of RB and of the d' ring), so the row-in-group, the ring rows
+// and which group holds a row are compile-time; only the group slot bases
+// (gb[0] for the group of row m, gb[1] the one before, ...) are registers.
+template <typename T, int TX, int KIND>
+struct K1Unit {
   using G = K1Geom<T, TX>;
-  constexpr int NT = G::NT;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
-  uint64_t *empty = full + G::NST;
-  volatile int *ctl = reinterpret_cast<volatile int *>(smem_raw + 224);   // abort, -, consumed, last row per producer
-  unsigned char *ring_b = smem_raw + 256;
-  const T *ring = reinterpret_cast<const T *>(ring_b);
-  T *dn = reinterpret_cast<T *>(ring_b + sizeof(T) * (size_t)G::NST * G::SLOT);
+  static constexpr int kind = KIND;
+  static constexpr int RB = G::RB, NSG = G::NSG, ESZ = (int)sizeof(T);
+  static constexpr int WIN = 4;                              // rows m-3 .. m are read by a step
+  static constexpr int NGB = (WIN - 1 + RB - 1) / RB + 1;    // groups those rows can span
+  static_assert(8 % RB == 0 && 8 % G::NDN == 0, "unroll by 8");
+  __device__ static constexpr int gback(int K, int k) { return fdiv(K, RB) - fdiv(K - k, RB); }
+
+  const unsigned char *ring_lo, *ring_hi;   // ring bounds (+ this thread's column)
+  const unsigned char *gb[NGB];
+  const unsigned char *next_sb;
+  T *dn;                                    // d' ring (+ this thread's column)
+  uint64_t *full, *empty;
+  const volatile int *abort;
+  T *d_out, *x_out, *q_out, *r_out;
+  uint64_t timeout_ns;
+  uint32_t fslot, fpar, eslot;
+  int tid, mlo, nr1, nrows, pitch, ng, nseen, nrel;
+  bool col_ok;
+  ColStore<T> cs;
+  T beta, pend;
+  DotAcc<T> dot0, dot1;
+
+  __device__ __forceinline__ void begin(const unsigned char *ring, uint32_t gbase) {
+    ring_lo = ring + tid * ESZ;
+    ring_hi = ring_lo + (size_t)NSG * G::GROUP;
+    fslot = gbase % NSG;
+    fpar = (gbase / NSG) & 1u;
+    eslot = fslot;
+    next_sb = ring_lo + (size_t)fslot * G::GROUP;
+#pragma unroll
+    for (int j = 0; j < NGB; ++j) gb[j] = next_sb;
+    nseen = 0;
+    nrel = 0;
+  }
+  template <int F>
+  __device__ __forceinline__ static const T *fld(const unsigned char *sb, int irow, int w) {
+    return reinterpret_cast<const T *>(sb + F) + irow * w;
+  }
+
+  template <int K>
+  __device__ __forceinline__ bool step(int rel) {
+    constexpr int I = K % RB;
+    if constexpr (I == 0) {
+#pragma unroll
+      for (int j = NGB - 1; j > 0; --j) gb[j] = gb[j - 1];
+      gb[0] = next_sb;
+      next_sb += G::GROUP;
+      if (next_sb == ring_hi) next_sb = ring_lo;
+    }
+    // Loads of a step come before its shared-memory stores: q on row m - 2
+    // first (it reads d' rows written in earlier steps), then d' on row m.
+    // q = A d' on row r = m - 2 (rel - 3 = r - j0)
+    if (rel >= 3 && rel - 3 < nrows && col_ok) {
+      const unsigned char *br = gb[gback(K, 2)], *bs = gb[gback(K, 3)];
+      constexpr int IR = pmod(K - 2, RB), IS = pmod(K - 3, RB);
+      const T *dr = dn + pmod(K - 2, G::NDN) * G::WDN;
+      const T *ds = dn + pmod(K - 3, G::NDN) * G::WDN;
+      const T *dnn = dn + pmod(K - 1, G::NDN) * G::WDN;
+      const T *Nr = fld<G::OFF_N>(br, IR, G::WT), *Ns = fld<G::OFF_N>(bs, IS, G::WT);
+      const T *Er = fld<G::OFF_E>(br, IR, G::WE), *Ar = fld<G::OFF_A>(br, IR, G::WT);
+      const T *Xr = fld<G::OFF_X>(br, IR, G::WT), *Dr = fld<G::OFF_D>(br, IR, G::WS);
+      const T c_ctr = dr[1];
+      T av = -Ns[0] * ds[1];
+      av = fma(-Er[G::H - 1], dr[0], av);
+      av = fma(Ar[0], c_ctr, av);
+      av = fma(-Er[G::H], dr[2], av);
+      av = fma(-Nr[0], dnn[1], av);
+      const size_t ro = (size_t)(mlo + rel - 2) * pitch;
+      if (kind == K1_ITER) {
+        const T xv = fma(pend, Dr[G::H], Xr[0]);
+        cs.put(d_out + ro, c_ctr);
+        cs.put(x_out + ro, xv);
+        cs.put(q_out + ro, av);
+        dot0.add(c_ctr, av);
+      } else if (kind == K1_SPMV) {
+        cs.put(q_out + ro, av);
+      } else {
+        const T bv = Xr[0];
+        const T rv = bv - av;
+        cs.put(r_out + ro, rv);
+        dot0.add(rv, rv);
+        dot1.add(bv, bv);
+      }
+    }
+    // last: d' on row m (the only part that waits for streamed data)
+    bool got = true, waited = false;
+    if (rel <= nr1) {                                  // row m = mlo + rel is streamed
+      if constexpr (I == 0) {
+        got = mbar_wait_or_abort(&full[fslot], fpar, timeout_ns, abort);
+        waited = true;
+        if (++fslot == (uint32_t)NSG) { fslot = 0; fpar ^= 1u; }
+      }
+      const T *S = fld<G::OFF_S>(gb[0], I, G::WS), *D = fld<G::OFF_D>(gb[0], I, G::WS);
+      T *dnm = dn + (K & (G::NDN - 1)) * G::WDN;
+      // d' on row m over columns [i0-1, i0+TX+1)
+      T v = S[G::H - 1];
+      if (kind == K1_ITER) v = fma(beta, D[G::H - 1], v);
+      dnm[0] = v;
+      if (tid < G::WDN - TX) {
+        T v2 = S[G::H - 1 + TX];
+        if (kind == K1_ITER) v2 = fma(beta, D[G::H - 1 + TX], v2);
+        dnm[TX] = v2;
+      }
+    }
+    if (!compute_sync_and<TX>(got)) return false;
+    if (waited) ++nseen;
+    // row m - 3 is finished: at the last row of its group, release the group
+    if constexpr (pmod(K - 2, RB) == 0) {
+      if (rel >= 3) {
+        if (tid == 0) mbar_arrive(&empty[eslot]);
+        if (++eslot == (uint32_t)NSG) eslot = 0;
+        ++nrel;
+      }
+    }
+    return true;
+  }
+
+  // All steps of the unit (rel = 0 .. nrows + 2); releases the unit's groups.
+  __device__ __forceinline__ bool run() {
+    const int last = nrows + 2;
+    for (int b = 0; b <= last; b += 8) {
+#define PCG_K1_STEP(K) \
+  if (b + K > last) break; \
+  if (!step<K>(b + K)) return false;
+      PCG_K1_STEP(0) PCG_K1_STEP(1) PCG_K1_STEP(2) PCG_K1_STEP(3)
+      PCG_K1_STEP(4) PCG_K1_STEP(5) PCG_K1_STEP(6) PCG_K1_STEP(7)
+#undef PCG_K1_STEP
+    }
+    for (; nrel < ng; ++nrel) {
+      if (tid == 0) mbar_arrive(&empty[eslot]);
+      if (++eslot == (uint32_t)NSG) eslot = 0;
+    }
+    return true;
+  }
+};
+
+template <typename T, int TX, int KIND>
+__global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
+  using G = K1Geom<T, TX>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = align128(smem_raw);
+  const RingCtl<G::NSG> rc(base);
+  T *dn = reinterpret_cast<T *>(rc.ring + (size_t)G::NSG * G::GROUP);
   double *red = reinterpret_cast<double *>(dn + (size_t)G::NDN * G::WDN);
-  int *flag = reinterpret_cast<int *>(red + 2 * (NT / 32));
-
-  const Unit un = p.units[blockIdx.x];
-  const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
-  SolveState *st = gdp->st;
-  LaunchState *ls = p.ls;
-  const int kind = p.kind;
+  constexpr int kind = KIND;
   const int tid = threadIdx.x;
-
-  if ((kind == K1_ITER || kind == K1_RESID_INIT) && *(volatile int32_t *)&st->done) return;
-  if (kind == K1_RESID_CHECK && *(volatile int32_t *)&st->retired) return;
-
-  const int nx = gdp->nx, ny = gdp->ny, pitch = gdp->pitch, ty = gdp->ty;
-  const int i0 = un.sx * TX, j0 = un.sy * ty;
-  const int rend = min(j0 + ty, ny);
-  const int mlo = j0 - 1, mhi = rend;          // rows streamed: south halo row .. north look-ahead row
-  const int dsel = st->dsel, rsel = st->rsel;
-  const size_t pitch_b = (size_t)pitch * sizeof(T);
-  constexpr int SLOTB = G::SLOT * (int)sizeof(T);
+  LaunchState *ls = p.ls;
 
   if (tid == 0) {
-    for (int s = 0; s < G::NST; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    ctl[0] = 0; ctl[1] = mlo - 1; ctl[2] = mlo - 1;
-    for (int w = 0; w < G::NPW; ++w) ctl[3 + w] = mlo - 1;
+    for (int s = 0; s < G::NSG; ++s) { mbar_init(&rc.full[s], 1); mbar_init(&rc.empty[s], 1); }
+    rc.ctl[CTL_ABORT] = 0; rc.ctl[CTL_ARMED] = 0; rc.ctl[CTL_SEEN] = 0; rc.ctl[CTL_FLAG] = 0;
     fence_mbar_init();
   }
   __syncthreads();
 
-  double acc0 = 0.0, acc1 = 0.0;
-  DotAcc<T> dot0, dot1;
+  auto skip_unit = [&](const SolveState *st) {
+    if (kind == K1_ITER || kind == K1_RESID_INIT) return *(const volatile int32_t *)&st->done != 0;
+    if (kind == K1_RESID_CHECK) return *(const volatile int32_t *)&st->retired != 0;
+    return false;
+  };
+
   if (tid >= TX) {
-    // ---- producer warps
-    const int lane = (tid - TX) & 31, pw = (tid - TX) >> 5;
-    RowCopy c{nullptr, 0, 0, 0};
-    const T *src = (kind == K1_ITER) ? gdp->s : (kind == K1_SPMV) ? gdp->d[0] : gdp->x;
-    auto at = [&](const T *plane, int col) { return reinterpret_cast<const char *>(plane + i0 + col); };
-    switch (lane) {
-      case 0: c = RowCopy{at(src, -G::H), (uint32_t)(G::OFF_S * sizeof(T)), (uint32_t)(G::WS * sizeof(T)), 0}; break;
-      case 1: if (kind == K1_ITER) c = RowCopy{at(gdp->d[dsel], -G::H), (uint32_t)(G::OFF_D * sizeof(T)), (uint32_t)(G::WS * sizeof(T)), 0}; break;
-      case 2: c = RowCopy{at(gdp->cn, 0), (uint32_t)(G::OFF_N * sizeof(T)), (uint32_t)(G::WT * sizeof(T)), 1}; break;
-      case 3: c = RowCopy{at(gdp->ce, -G::H), (uint32_t)(G::OFF_E * sizeof(T)), (uint32_t)(G::WE * sizeof(T)), 2}; break;
-      case 4: c = RowCopy{at(gdp->a, 0), (uint32_t)(G::OFF_A * sizeof(T)), (uint32_t)(G::WT * sizeof(T)), 2}; break;
-      case 5: if (kind != K1_SPMV) c = RowCopy{at(kind == K1_ITER ? gdp->x : gdp->b, 0), (uint32_t)(G::OFF_X * sizeof(T)), (uint32_t)(G::WT * sizeof(T)), 2}; break;
-      default: break;
+    // ---- producer warp
+    const int lane = tid - TX;
+    uint32_t gq = 0;
+    int last_g = -1;
+    for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
+      const Unit un = p.units[ui];
+      const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
+      if (skip_unit(gdp->st)) continue;
+      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
+      const int mlo = j0 - 1, mhi = min(j0 + gdp->ty, gdp->ny);
+      const int ng = (mhi - mlo + G::RB) / G::RB;
+      const int dsel = gdp->st->dsel;
+      const T *src_s = (kind == K1_ITER) ? gdp->s : (kind == K1_SPMV) ? gdp->d[0] : gdp->x;
+      const int tm_s = (kind == K1_ITER) ? TM_WS_S : (kind == K1_SPMV) ? TM_WS_D0 : TM_WS_X;
+      const TensorMapBytes *tm = reinterpret_cast<const TensorMapBytes *>(gdp->tm);
+      const int gx = 128 / (int)sizeof(T);
+      auto mk = [&](const T *plane, int tmi, int col, int off, int w) {
+        FieldCopy c;
+        c.src = reinterpret_cast<const char *>(plane + i0 + col);
+        c.tmap = tm ? (const void *)(tm + tmi) : nullptr;
+        c.x = gx + i0 + col;
+        c.dst = (uint32_t)off;
+        c.bytes = (uint32_t)(G::RB * w * (int)sizeof(T));
+        return c;
+      };
+      FieldCopy c{};
+      bool has = true;
+      switch (lane) {
+        case 0: c = mk(src_s, tm_s, -G::H, G::OFF_S, G::WS); break;
+        case 1: c = mk(gdp->d[dsel], dsel ? TM_WS_D1 : TM_WS_D0, -G::H, G::OFF_D, G::WS); has = kind == K1_ITER; break;
+        case 2: c = mk(gdp->cn, TM_WT_CN, 0, G::OFF_N, G::WT); break;
+        case 3: c = mk(gdp->ce, TM_WE_CE, -G::H, G::OFF_E, G::WE); break;
+        case 4: c = mk(gdp->a, TM_WT_A, 0, G::OFF_A, G::WT); break;
+        case 5: c = mk(kind == K1_ITER ? gdp->x : gdp->b, kind == K1_ITER ? TM_WT_X : TM_WT_B, 0, G::OFF_X, G::WT);
+                has = kind != K1_SPMV; break;
+        default: has = false; break;
+      }
+      const bool skip_first = (p.dbg_skip_unit == ui) && lane == 0;
+      if (!produce_unit<G::NSG, G::RB>(c, has, rc.ring, G::GROUP, rc.full, rc.empty, mlo, ng, gq,
+                                       (size_t)gdp->pitch * sizeof(T), skip_first, un.g != last_g, p.timeout_ns, rc.ctl))
+        break;
+      last_g = un.g;
     }
-    const bool skip_first = (p.dbg_skip_unit == (int)blockIdx.x) && lane == 0 && pw == 0;
-    const int last = produce_rows<G::NST>(c, ring_b, SLOTB, full, empty, mlo, mhi, pitch_b, j0, skip_first,
-                                          p.timeout_ns, ctl, pw, G::NPW);
-    if (lane == 0) ctl[3 + pw] = last;
+    if (lane == 0) rc.ctl[CTL_ARMED] = (int)gq;
   } else {
     // ---- compute threads
-    const T beta = (kind == K1_ITER) ? (T)st->beta : (T)0;
-    const T pend = (kind == K1_ITER) ? (T)st->pending : (T)0;
-    T *const d_out = gdp->d[dsel ^ 1];
-    T *const x_out = gdp->x;
-    T *const q_out = gdp->q;
-    T *const r_out = gdp->r[rsel];
-    int consumed = mlo - 1;
-    for (int m = mlo; m <= mhi + 1; ++m) {
-      bool got = true;
-      if (m <= mhi) {
-        const int slot = (m - mlo) & (G::NST - 1);
-        got = mbar_wait_bounded(&full[slot], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
-        const T *sl = ring + (size_t)slot * G::SLOT;
-        T *dnm = dn + (size_t)((m + 8) & (G::NDN - 1)) * G::WDN;
-        // d' on row m over columns [i0-1, i0+TX+1)
-        for (int c = tid; c < G::WDN; c += TX) {
-          const int k = c - 1 + G::H;
-          T v = sl[G::OFF_S + k];
-          if (kind == K1_ITER) v = fma(beta, sl[G::OFF_D + k], v);
-          dnm[c] = v;
-        }
+    uint32_t gbase = 0, seen = 0;
+    bool aborted = false;
+    for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
+      const Unit un = p.units[ui];
+      const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
+      SolveState *st = gdp->st;
+      if (skip_unit(st)) continue;
+      const int nx = gdp->nx, ny = gdp->ny;
+      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
+      const int rend = min(j0 + gdp->ty, ny);
+      const int mlo = j0 - 1, mhi = rend;
+      const int ng = (mhi - mlo + G::RB) / G::RB;
+      double acc0 = 0.0, acc1 = 0.0;
+      if (!aborted) {
+        K1Unit<T, TX, KIND> cx;
+        cx.tid = tid; cx.dn = dn + tid; cx.full = rc.full; cx.empty = rc.empty; cx.abort = &rc.ctl[CTL_ABORT];
+        cx.timeout_ns = p.timeout_ns;
+        cx.begin(rc.ring, gbase);
+        cx.mlo = mlo; cx.nr1 = mhi - mlo; cx.nrows = rend - j0; cx.ng = ng;
+        cx.pitch = gdp->pitch;
+        cx.col_ok = i0 + tid < nx;
+        cx.cs.init(i0 + tid, nx);
+        cx.beta = (kind == K1_ITER) ? (T)st->beta : (T)0;
+        cx.pend = (kind == K1_ITER) ? (T)st->pending : (T)0;
+        const int dsel = st->dsel;
+        cx.d_out = gdp->d[dsel ^ 1]; cx.x_out = gdp->x; cx.q_out = gdp->q; cx.r_out = gdp->r[st->rsel];
+        if (!cx.run()) aborted = true;
+        seen = gbase + (uint32_t)cx.nseen;
+        acc0 = cx.dot0.total();
+        acc1 = cx.dot1.total();
       }
-      const int r = m - 2;
-      if (r >= j0 && r < rend) {
-        const int col = i0 + tid;
-        if (col < nx) {
-          const T *slr = ring + (size_t)((r - mlo) & (G::NST - 1)) * G::SLOT;
-          const T *sls = ring + (size_t)((r - 1 - mlo) & (G::NST - 1)) * G::SLOT;
-          const T *dr = dn + (size_t)((r + 8) & (G::NDN - 1)) * G::WDN;
-          const T *ds = dn + (size_t)((r - 1 + 8) & (G::NDN - 1)) * G::WDN;
-          const T *dnn = dn + (size_t)((r + 1 + 8) & (G::NDN - 1)) * G::WDN;
-          const T c_ctr = dr[tid + 1];
-          T av = -sls[G::OFF_N + tid] * ds[tid + 1];
-          av = fma(-slr[G::OFF_E + G::H + tid - 1], dr[tid], av);
-          av = fma(slr[G::OFF_A + tid], c_ctr, av);
-          av = fma(-slr[G::OFF_E + G::H + tid], dr[tid + 2], av);
-          av = fma(-slr[G::OFF_N + tid], dnn[tid + 1], av);
-          const size_t ro = (size_t)r * pitch;
+      gbase += ng;
+      if (aborted && tid == 0) { rc.ctl[CTL_ABORT] = 1; flag_timeout(st); }
+      if (kind == K1_SPMV) continue;
+      if (unit_reduce2<TX>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt1, red, &rc.ctl[CTL_FLAG])) {
+        if (tid == 0) {
           if (kind == K1_ITER) {
-            const T xv = fma(pend, slr[G::OFF_D + G::H + tid], slr[G::OFF_X + tid]);
-            store_dup(d_out + ro, col, nx, c_ctr);
-            store_dup(x_out + ro, col, nx, xv);
-            store_dup(q_out + ro, col, nx, av);
-            dot0.add(c_ctr, av);
-          } else if (kind == K1_SPMV) {
-            store_dup(q_out + ro, col, nx, av);
+            const double dq = acc0;
+            st->dq = dq;
+            st->pending = 0.0;
+            st->dsel = st->dsel ^ 1;
+            if (st->status != PCG_OK) grid_finished(st, ls, PCG_OK, false, p);
+            else if (!(dq > 0.0) || !isfinite(dq)) grid_finished(st, ls, PCG_EBREAKDOWN, false, p);
+            else st->alpha = st->rho / dq;
+          } else if (kind == K1_RESID_INIT) {
+            st->rr = acc0;
+            st->bb = acc1;
+            if (st->status != PCG_OK) grid_finished(st, ls, PCG_OK, false, p);
+            else if (!isfinite(acc1) || !isfinite(acc0)) grid_finished(st, ls, PCG_EBREAKDOWN, false, p);
+            else if (acc1 == 0.0) { st->bzero = 1; grid_finished(st, ls, PCG_OK, false, p); }
           } else {
-            const T bv = slr[G::OFF_X + tid];
-            const T rv = bv - av;
-            store_dup(r_out + ro, col, nx, rv);
-            dot0.add(rv, rv);
-            dot1.add(bv, bv);
+            st->rr_true = acc0;
           }
         }
       }
-      if (!compute_sync_and<TX>(got)) {
-        if (tid == 0) { ctl[0] = 1; flag_timeout(st); }
-        break;
-      }
-      if (m <= mhi) consumed = m;
-      // row m-3 is finished: its slot may be refilled
-      if (tid == 0 && m - 3 >= mlo && m - 3 + G::NST <= mhi) mbar_arrive(&empty[(m - 3 - mlo) & (G::NST - 1)]);
     }
-    if (tid == 0) ctl[2] = consumed;
-    acc0 = dot0.total();
-    acc1 = dot1.total();
+    if (tid == 0) rc.ctl[CTL_SEEN] = (int)seen;
   }
   __syncthreads();
-  if (tid == 0 && ctl[0]) {
-    // the compute threads gave up: wait (bounded) for the rows still in flight
-    for (int w = 0; w < G::NPW; ++w)
-      for (int m = mlo + w; m <= ctl[3 + w]; m += G::NPW)
-        if (m > ctl[2])
-          mbar_wait_bounded(&full[(m - mlo) & (G::NST - 1)], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
-  }
-  if (kind == K1_SPMV) return;
-  if (grid_reduce2<NT>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt1, red, flag)) {
-    if (threadIdx.x == 0) {
-      if (kind == K1_ITER) {
-        const double dq = acc0;
-        st->dq = dq;
-        st->pending = 0.0;
-        st->dsel = dsel ^ 1;
-        if (st->status != PCG_OK) grid_finished(st, ls, PCG_OK, false, p);
-        else if (!(dq > 0.0) || !isfinite(dq)) grid_finished(st, ls, PCG_EBREAKDOWN, false, p);
-        else st->alpha = st->rho / dq;
-      } else if (kind == K1_RESID_INIT) {
-        st->rr = acc0;
-        st->bb = acc1;
-        if (st->status != PCG_OK) grid_finished(st, ls, PCG_OK, false, p);
-        else if (!isfinite(acc1) || !isfinite(acc0)) grid_finished(st, ls, PCG_EBREAKDOWN, false, p);
-        else if (acc1 == 0.0) { st->bzero = 1; grid_finished(st, ls, PCG_OK, false, p); }
-      } else {
-        st->rr_true = acc0;
-      }
-    }
-  }
+  drain_groups<G::NSG>(rc, p.timeout_ns);
 }
 
 // ------------------------------------------------------------ kernel 2
@@ -533,202 +811,320 @@ struct K2Geom {
   static constexpr int WTC = TX + 2 * R;             // t computed on [i0-R, i0+TX+R)
   static constexpr int NRN = pow2_at_least(LD + 3);  // rows of r' kept (m-2-LD .. m)
   static constexpr int NTT = pow2_at_least(LD + 2);  // rows of t kept (m-2-LD .. m-1)
-  // rows streamed ahead: binary64 is bound by the FP64 pipe, so shared memory
-  // goes to CTAs (latency hiding for the FP64 work); binary32 is bound by
-  // HBM, so it goes to rows in flight
-  // ring slots: rows m-2-LD .. m live plus rows in flight. binary64 is bound
-  // by the FP64 pipe, so its shared memory goes to CTAs (one row ahead);
-  // binary32 is bound by HBM, so it keeps more rows in flight.
-  static constexpr int NST = sizeof(T) == 8 ? LD + 4 : pow2_at_least(LD + 5);
-  __device__ static constexpr int slot(int x) { return (NST & (NST - 1)) == 0 ? (x & (NST - 1)) : (x % NST); }
-  static constexpr int NPW = 1;                      // producer warps
-  static constexpr int NT = TX + 32 * NPW;           // compute threads + producer warps
-  static constexpr int OFF_R = 0, OFF_Q = WR, OFF_Z = 2 * WR, OFF_DI = 2 * WR + NZ * WZ, SLOT = OFF_DI + WZ;
-  static constexpr size_t SMEM =
-      256 + sizeof(T) * ((size_t)NST * SLOT + (size_t)NRN * WRC + (size_t)NTT * WTC) + 16 * (NT / 32) + 64;
-  static_assert(2 * NST * 8 <= 224 && 3 + NPW <= 8, "barrier / control area of the first 256 bytes");
+  static constexpr int RB = sizeof(T) == 4 ? 2 : 1;  // rows per group
+  static constexpr int FA = RB > 1 ? 128 : 16;
+  __host__ __device__ static constexpr int fb(int w) { return round_up_c(RB * w * (int)sizeof(T), FA); }
+  static constexpr int OFF_R = 0, OFF_Q = fb(WR), OFF_Z = 2 * fb(WR), OFF_DI = OFF_Z + NZ * fb(WZ),
+                       GROUP = OFF_DI + fb(WZ);      // bytes
+  // group slots: the groups a step reads (rows m-2-LD..m) plus at least one
+  // in flight. Both precisions are bound by their compute warps, so shared
+  // memory goes to CTAs per SM: binary64 keeps one row ahead, binary32 about
+  // 42 KB of ring.
+  static constexpr int LIVE = (LD + 2 + RB - 1) / RB + 1;
+  static constexpr int NSG = RB == 1 ? LD + 4 : ring_groups(42000, GROUP, LIVE);
+  static constexpr int NT = TX + 32;
+  static constexpr size_t SMEM = 128 + 256 + (size_t)NSG * GROUP +
+                                 sizeof(T) * ((size_t)NRN * WRC + (size_t)NTT * WTC) + 16 * (NT / 32) + 64;
 };
 
-template <typename T, int TX, class P>
-__global__ void __launch_bounds__(TX + 32 * K2Geom<T, TX, P>::NPW) k_precond(KParams p) {
+// One unit of k_precond on the compute side, unrolled by 8 steps like K1Unit.
+template <typename T, int TX, class P, int KIND>
+struct K2Unit {
   using G = K2Geom<T, TX, P>;
-  constexpr int R = P::R, LD = P::LD, NZ = P::NZ, NW = P::NW, NT = G::NT;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
-  uint64_t *empty = full + G::NST;
-  volatile int *ctl = reinterpret_cast<volatile int *>(smem_raw + 224);
-  unsigned char *ring_b = smem_raw + 256;
-  const T *ring = reinterpret_cast<const T *>(ring_b);
-  T *rn = reinterpret_cast<T *>(ring_b + sizeof(T) * (size_t)G::NST * G::SLOT);
+  static constexpr int kind = KIND;
+  static constexpr int R = P::R, LD = P::LD, NZ = P::NZ, NW = P::NW;
+  static constexpr int RB = G::RB, NSG = G::NSG, ESZ = (int)sizeof(T);
+  static constexpr int WIN = LD + 3;                         // rows m-2-LD .. m are read by a step
+  static constexpr int NGB = (WIN - 1 + RB - 1) / RB + 1;
+  static constexpr int FBZ = G::fb(G::WZ);
+  static_assert(8 % RB == 0 && 8 % G::NRN == 0 && 8 % G::NTT == 0, "unroll by 8");
+  __device__ static constexpr int gback(int K, int k) { return fdiv(K, RB) - fdiv(K - k, RB); }
+
+  const unsigned char *ring_lo, *ring_hi;
+  const unsigned char *gb[NGB];
+  const unsigned char *next_sb;
+  T *rn, *tt;                              // rings (+ this thread's column)
+  uint64_t *full, *empty;
+  const volatile int *abort;
+  T *rout, *s_out;
+  const T *zwrap;
+  uint64_t timeout_ns;
+  uint32_t fslot, fpar, eslot;
+  int tid, nx, ny, mlo, j0, i0, nr1, nrows, pitch, ng, nseen, nrel, col;
+  bool col_ok, edge;
+  ColStore<T> cs;
+  T alpha;
+  DotAcc<T> dot0, dot1;
+
+  __device__ __forceinline__ void begin(const unsigned char *ring, uint32_t gbase) {
+    ring_lo = ring + tid * ESZ;
+    ring_hi = ring_lo + (size_t)NSG * G::GROUP;
+    fslot = gbase % NSG;
+    fpar = (gbase / NSG) & 1u;
+    eslot = fslot;
+    next_sb = ring_lo + (size_t)fslot * G::GROUP;
+#pragma unroll
+    for (int j = 0; j < NGB; ++j) gb[j] = next_sb;
+    nseen = 0;
+    nrel = 0;
+  }
+  __device__ __forceinline__ static const T *fld(const unsigned char *sb, int off, int irow, int w) {
+    return reinterpret_cast<const T *>(sb + off) + irow * w;
+  }
+
+  // t = D^-1 (Z^T r') on row mt (phase KT = K - 1) at column c = tid + dc of
+  // [i0-R, i0+TX+R): dc = 0 (main) or TX (the right halo columns)
+  template <int KT>
+  __device__ __forceinline__ T tcol(const unsigned char *bz, int dc, int mt) const {
+    constexpr int IZ = pmod(KT, RB);
+    const T *rnt = rn + pmod(KT, G::NRN) * G::WRC + dc;
+    T acc = rnt[R];
+#pragma unroll
+    for (int s = 0; s < NZ; ++s) {
+      const T *rrow = rn + pmod(KT + P::dy(s), G::NRN) * G::WRC + dc;
+      acc = fma(fld(bz, G::OFF_Z + s * FBZ, IZ, G::WZ)[G::HZ - R + dc], rrow[R + P::dx(s)], acc);
+    }
+    if (edge && mt < ny) {                   // rows >= ny: zero t (Z, D^-1 and r' are zero there)
+      const int cg = i0 - R + tid + dc;
+      const int cm = cg < 0 ? cg + nx : (cg >= nx ? cg - nx : cg);
+#pragma unroll
+      for (int w = 0; w < (NW > 0 ? NW : 1); ++w)
+        if (cm == nx - 1 - P::wcol(w)) acc = fma(zwrap[(size_t)mt * NW + w], rnt[R + P::wdx(w)], acc);
+    }
+    return acc * fld(bz, G::OFF_DI, IZ, G::WZ)[G::HZ - R + dc];
+  }
+
+  template <int K>
+  __device__ __forceinline__ bool step(int rel) {
+    constexpr int I = K % RB;
+    if constexpr (I == 0) {
+#pragma unroll
+      for (int j = NGB - 1; j > 0; --j) gb[j] = gb[j - 1];
+      gb[0] = next_sb;
+      next_sb += G::GROUP;
+      if (next_sb == ring_hi) next_sb = ring_lo;
+    }
+    // Loads of a step come before its shared-memory stores: s on row
+    // m - 2 - LD (reads t rows of earlier steps), t on row m - 1 (reads r'
+    // rows of earlier steps), then r' on row m, the only part that waits for
+    // streamed data.
+    // s = Z t on row r = m - 2 - LD (rel - 2 - 2 LD = r - j0)
+    if (rel - 2 - 2 * LD >= 0 && rel - 2 - 2 * LD < nrows && col_ok) {
+      constexpr int KR = K - 2 - LD;
+      const T *tr = tt + pmod(KR, G::NTT) * G::WTC;
+      T acc = tr[R];
+#pragma unroll
+      for (int s = 0; s < NZ; ++s) {
+        // row r - dy(s) holds the column whose Z entry reaches (col, r)
+        const int kz = KR - P::dy(s);
+        const unsigned char *bz = gb[gback(K, 2 + LD + P::dy(s))];
+        const T *trow = tt + pmod(kz, G::NTT) * G::WTC;
+        acc = fma(fld(bz, G::OFF_Z + s * FBZ, pmod(kz, RB), G::WZ)[G::HZ - P::dx(s)], trow[R - P::dx(s)], acc);
+      }
+      const int r = mlo + rel - 2 - LD;
+      if (edge) {
+#pragma unroll
+        for (int w = 0; w < (NW > 0 ? NW : 1); ++w) {
+          const int target = P::wdx(w) - 1 - P::wcol(w);   // 0 or 1
+          if (col == target) acc = fma(zwrap[(size_t)r * NW + w], tr[R - P::wdx(w)], acc);
+        }
+      }
+      const T rv = rn[pmod(KR, G::NRN) * G::WRC + 2 * R];
+      const size_t ro = (size_t)r * pitch;
+      cs.put(s_out + ro, acc);
+      if (kind != K2_APPLY) cs.put(rout + ro, rv);
+      dot0.add(acc, rv);
+      dot1.add(rv, rv);
+    }
+    // t on row mt = m - 1 (rel - 1 - LD = mt - j0)
+    if (rel - 1 - LD >= 0 && rel - 1 <= nr1) {
+      const unsigned char *bz = gb[gback(K, 1)];
+      const int mt = mlo + rel - 1;
+      T *tm = tt + pmod(K - 1, G::NTT) * G::WTC;
+      tm[0] = tcol<K - 1>(bz, 0, mt);
+      if (tid < G::WTC - TX) tm[TX] = tcol<K - 1>(bz, TX, mt);
+    }
+    bool got = true, waited = false;
+    // r' on row m over [i0-2R, i0+TX+2R)
+    if (rel <= nr1) {
+      if constexpr (I == 0) {
+        got = mbar_wait_or_abort(&full[fslot], fpar, timeout_ns, abort);
+        waited = true;
+        if (++fslot == (uint32_t)NSG) { fslot = 0; fpar ^= 1u; }
+      }
+      const T *Rr = fld(gb[0], G::OFF_R, I, G::WR), *Qr = fld(gb[0], G::OFF_Q, I, G::WR);
+      T *rnm = rn + (K & (G::NRN - 1)) * G::WRC;
+      constexpr int k0 = G::HR - 2 * R;
+      T v = Rr[k0];
+      if (kind == K2_ITER) v = fma(-alpha, Qr[k0], v);
+      rnm[0] = v;
+      if (tid < G::WRC - TX) {
+        T v2 = Rr[k0 + TX];
+        if (kind == K2_ITER) v2 = fma(-alpha, Qr[k0 + TX], v2);
+        rnm[TX] = v2;
+      }
+    }
+    if (!compute_sync_and<TX>(got)) return false;
+    if (waited) ++nseen;
+    // row m - 2 - LD is finished: at the last row of its group, release the group
+    if constexpr (pmod(K - 1 - LD, RB) == 0) {
+      if (rel - 2 - LD >= 0) {
+        if (tid == 0) mbar_arrive(&empty[eslot]);
+        if (++eslot == (uint32_t)NSG) eslot = 0;
+        ++nrel;
+      }
+    }
+    return true;
+  }
+
+  // All steps of the unit (rel = 0 .. nrows + 2 LD + 1); releases the unit's groups.
+  __device__ __forceinline__ bool run() {
+    const int last = nrows + 2 * LD + 1;
+    for (int b = 0; b <= last; b += 8) {
+#define PCG_K2_STEP(K) \
+  if (b + K > last) break; \
+  if (!step<K>(b + K)) return false;
+      PCG_K2_STEP(0) PCG_K2_STEP(1) PCG_K2_STEP(2) PCG_K2_STEP(3)
+      PCG_K2_STEP(4) PCG_K2_STEP(5) PCG_K2_STEP(6) PCG_K2_STEP(7)
+#undef PCG_K2_STEP
+    }
+    for (; nrel < ng; ++nrel) {
+      if (tid == 0) mbar_arrive(&empty[eslot]);
+      if (++eslot == (uint32_t)NSG) eslot = 0;
+    }
+    return true;
+  }
+};
+
+template <typename T, int TX, class P, int KIND>
+__global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
+  using G = K2Geom<T, TX, P>;
+  constexpr int R = P::R, LD = P::LD, NZ = P::NZ, NW = P::NW;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char *base = align128(smem_raw);
+  const RingCtl<G::NSG> rc(base);
+  T *rn = reinterpret_cast<T *>(rc.ring + (size_t)G::NSG * G::GROUP);
   T *tt = rn + (size_t)G::NRN * G::WRC;
   double *red = reinterpret_cast<double *>(tt + (size_t)G::NTT * G::WTC);
-  int *flag = reinterpret_cast<int *>(red + 2 * (NT / 32));
-
-  const Unit un = p.units[blockIdx.x];
-  const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
-  SolveState *st = gdp->st;
-  LaunchState *ls = p.ls;
-  const int kind = p.kind;
+  constexpr int kind = KIND;
   const int tid = threadIdx.x;
+  LaunchState *ls = p.ls;
 
   if (p.guard && blockIdx.x == 0 && tid == 0) loop_guard(ls, p);
-  if (kind != K2_APPLY && *(volatile int32_t *)&st->done) return;
-
-  const int nx = gdp->nx, ny = gdp->ny, pitch = gdp->pitch, ty = gdp->ty;
-  const int i0 = un.sx * TX, j0 = un.sy * ty;
-  const int rend = min(j0 + ty, ny);
-  const int mlo = j0 - LD, mhi = rend + LD - 1;
-  const int rsel = (kind == K2_APPLY) ? 0 : st->rsel;
-  const size_t pitch_b = (size_t)pitch * sizeof(T);
-  constexpr int SLOTB = G::SLOT * (int)sizeof(T);
-
   if (tid == 0) {
-    for (int s = 0; s < G::NST; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    ctl[0] = 0; ctl[1] = mlo - 1; ctl[2] = mlo - 1;
-    for (int w = 0; w < G::NPW; ++w) ctl[3 + w] = mlo - 1;
+    for (int s = 0; s < G::NSG; ++s) { mbar_init(&rc.full[s], 1); mbar_init(&rc.empty[s], 1); }
+    rc.ctl[CTL_ABORT] = 0; rc.ctl[CTL_ARMED] = 0; rc.ctl[CTL_SEEN] = 0; rc.ctl[CTL_FLAG] = 0;
     fence_mbar_init();
   }
   __syncthreads();
 
-  double acc0 = 0.0, acc1 = 0.0;
-  DotAcc<T> dot0, dot1;
+  auto skip_unit = [&](const SolveState *st) {
+    return kind != K2_APPLY && *(const volatile int32_t *)&st->done != 0;
+  };
+
   if (tid >= TX) {
-    // ---- producer warps
-    const int lane = (tid - TX) & 31, pw = (tid - TX) >> 5;
-    auto at = [&](const T *plane, int col) { return reinterpret_cast<const char *>(plane + i0 + col); };
-    RowCopy c{nullptr, 0, 0, 0};
-    if (lane == 0) c = RowCopy{at(gdp->r[rsel], -G::HR), (uint32_t)(G::OFF_R * sizeof(T)), (uint32_t)(G::WR * sizeof(T)), 0};
-    else if (lane == 1) { if (kind == K2_ITER) c = RowCopy{at(gdp->q, -G::HR), (uint32_t)(G::OFF_Q * sizeof(T)), (uint32_t)(G::WR * sizeof(T)), 0}; }
-    else if (lane - 2 < NZ) c = RowCopy{at(gdp->z[lane - 2], -G::HZ), (uint32_t)((G::OFF_Z + (lane - 2) * G::WZ) * sizeof(T)), (uint32_t)(G::WZ * sizeof(T)), 3};
-    else if (lane - 2 == NZ) c = RowCopy{at(gdp->dinv, -G::HZ), (uint32_t)(G::OFF_DI * sizeof(T)), (uint32_t)(G::WZ * sizeof(T)), 3};
-    const bool skip_first = (p.dbg_skip_unit == (int)blockIdx.x) && lane == 0 && pw == 0;
-    const int last = produce_rows<G::NST>(c, ring_b, SLOTB, full, empty, mlo, mhi, pitch_b, j0, skip_first,
-                                          p.timeout_ns, ctl, pw, G::NPW);
-    if (lane == 0) ctl[3 + pw] = last;
+    // ---- producer warp
+    const int lane = tid - TX;
+    uint32_t gq = 0;
+    int last_g = -1;
+    for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
+      const Unit un = p.units[ui];
+      const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
+      if (skip_unit(gdp->st)) continue;
+      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
+      const int rend = min(j0 + gdp->ty, gdp->ny);
+      const int mlo = j0 - LD, mhi = rend + LD - 1;
+      const int ng = (mhi - mlo + G::RB) / G::RB;
+      const int rsel = (kind == K2_APPLY) ? 0 : gdp->st->rsel;
+      const TensorMapBytes *tm = reinterpret_cast<const TensorMapBytes *>(gdp->tm);
+      const int gx = 128 / (int)sizeof(T);
+      auto mk = [&](const T *plane, int tmi, int col, int off, int w) {
+        FieldCopy c;
+        c.src = reinterpret_cast<const char *>(plane + i0 + col);
+        c.tmap = tm ? (const void *)(tm + tmi) : nullptr;
+        c.x = gx + i0 + col;
+        c.dst = (uint32_t)off;
+        c.bytes = (uint32_t)(G::RB * w * (int)sizeof(T));
+        return c;
+      };
+      FieldCopy c{};
+      bool has = true;
+      if (lane == 0) c = mk(gdp->r[rsel], rsel ? TM_WR_R1 : TM_WR_R0, -G::HR, G::OFF_R, G::WR);
+      else if (lane == 1) { c = mk(gdp->q, TM_WR_Q, -G::HR, G::OFF_Q, G::WR); has = kind == K2_ITER; }
+      else if (lane - 2 < NZ) c = mk(gdp->z[lane - 2], TM_WZ_Z0 + lane - 2, -G::HZ, G::OFF_Z + (lane - 2) * G::fb(G::WZ), G::WZ);
+      else if (lane - 2 == NZ) c = mk(gdp->dinv, TM_WZ_DI, -G::HZ, G::OFF_DI, G::WZ);
+      else has = false;
+      const bool skip_first = (p.dbg_skip_unit == ui) && lane == 0;
+      if (!produce_unit<G::NSG, G::RB>(c, has, rc.ring, G::GROUP, rc.full, rc.empty, mlo, ng, gq,
+                                       (size_t)gdp->pitch * sizeof(T), skip_first, un.g != last_g, p.timeout_ns, rc.ctl))
+        break;
+      last_g = un.g;
+    }
+    if (lane == 0) rc.ctl[CTL_ARMED] = (int)gq;
   } else {
     // ---- compute threads
-    const T alpha = (kind == K2_ITER) ? (T)st->alpha : (T)0;
-    T *const rout = gdp->r[rsel ^ 1];
-    T *const s_out = gdp->s;
-    const T *const zwrap = gdp->zwrap;
-    // the strips holding the first or last columns apply the periodic side table
-    const bool edge = NW > 0 && (i0 < 2 * R + 2 || i0 + TX + 2 * R + 2 > nx);
-    int consumed = mlo - 1;
-    for (int m = mlo; m <= rend + LD + 1; ++m) {
-      bool got = true;
-      // r' on row m over [i0-2R, i0+TX+2R)
-      if (m <= mhi) {
-        const int slot = G::slot(m - mlo);
-        got = mbar_wait_bounded(&full[slot], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
-        const T *sl = ring + (size_t)slot * G::SLOT;
-        T *rnm = rn + (size_t)((m + 8) & (G::NRN - 1)) * G::WRC;
-        for (int c = tid; c < G::WRC; c += TX) {
-          const int k = c + G::HR - 2 * R;
-          T v = sl[G::OFF_R + k];
-          if (kind == K2_ITER) v = fma(-alpha, sl[G::OFF_Q + k], v);
-          rnm[c] = v;
+    uint32_t gbase = 0, seen = 0;
+    bool aborted = false;
+    for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
+      const Unit un = p.units[ui];
+      const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
+      SolveState *st = gdp->st;
+      if (skip_unit(st)) continue;
+      const int nx = gdp->nx, ny = gdp->ny;
+      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
+      const int rend = min(j0 + gdp->ty, ny);
+      const int mlo = j0 - LD, mhi = rend + LD - 1;
+      const int ng = (mhi - mlo + G::RB) / G::RB;
+      double acc0 = 0.0, acc1 = 0.0;
+      const int rsel = (kind == K2_APPLY) ? 0 : st->rsel;
+      if (!aborted) {
+        K2Unit<T, TX, P, KIND> cx;
+        cx.tid = tid; cx.rn = rn + tid; cx.tt = tt + tid; cx.full = rc.full; cx.empty = rc.empty;
+        cx.abort = &rc.ctl[CTL_ABORT]; cx.timeout_ns = p.timeout_ns;
+        cx.begin(rc.ring, gbase);
+        cx.nx = nx; cx.ny = ny; cx.mlo = mlo; cx.j0 = j0; cx.i0 = i0; cx.nr1 = mhi - mlo;
+        cx.nrows = rend - j0; cx.ng = ng; cx.pitch = gdp->pitch; cx.col = i0 + tid;
+        cx.col_ok = cx.col < nx;
+        cx.cs.init(cx.col, nx);
+        cx.alpha = (kind == K2_ITER) ? (T)st->alpha : (T)0;
+        cx.rout = gdp->r[rsel ^ 1]; cx.s_out = gdp->s; cx.zwrap = gdp->zwrap;
+        // the strips holding the first or last columns apply the periodic side table
+        cx.edge = NW > 0 && (i0 < 2 * R + 2 || i0 + TX + 2 * R + 2 > nx);
+        if (!cx.run()) aborted = true;
+        seen = gbase + (uint32_t)cx.nseen;
+        acc0 = cx.dot0.total();
+        acc1 = cx.dot1.total();
+      }
+      gbase += ng;
+      if (aborted && tid == 0) { rc.ctl[CTL_ABORT] = 1; flag_timeout(st); }
+      if (kind == K2_APPLY) continue;
+      if (unit_reduce2<TX>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt2, red, &rc.ctl[CTL_FLAG])) {
+        if (tid == 0) {
+          const double rho_new = acc0, rr = acc1;
+          st->rr = rr;
+          st->rsel = rsel ^ 1;
+          if (kind == K2_ITER) {
+            st->beta = rho_new / st->rho;
+            st->pending = st->alpha;
+            st->iter += 1;
+          } else {
+            st->beta = 0.0;
+            st->pending = 0.0;
+          }
+          st->rho = rho_new;
+          const double relres = sqrt(rr) / sqrt(st->bb);
+          if (st->status != PCG_OK) grid_finished(st, ls, PCG_OK, true, p);
+          else if (!isfinite(rho_new) || !isfinite(rr)) grid_finished(st, ls, PCG_EBREAKDOWN, true, p);
+          else if (!(relres > st->rtol)) grid_finished(st, ls, PCG_OK, true, p);
+          else if (st->iter >= st->max_iter) grid_finished(st, ls, PCG_ENOTCONV, true, p);
+          else if (!(rho_new > 0.0)) grid_finished(st, ls, PCG_EBREAKDOWN, true, p);
         }
       }
-      // t = D^-1 (Z^T r') on row mt = m - 1 over [i0-R, i0+TX+R)
-      const int mt = m - 1;
-      if (mt >= j0 && mt <= mhi) {
-        const T *sl = ring + (size_t)(G::slot(mt - mlo)) * G::SLOT;
-        const T *rnt = rn + (size_t)((mt + 8) & (G::NRN - 1)) * G::WRC;
-        T *tm = tt + (size_t)((mt + 8) & (G::NTT - 1)) * G::WTC;
-        for (int c = tid; c < G::WTC; c += TX) {
-          T acc = (T)0;
-          if (mt < ny) {
-            const int kz = c + G::HZ - R;
-            acc = rnt[c + R];
-#pragma unroll
-            for (int s = 0; s < NZ; ++s) {
-              const T *rrow = rn + (size_t)((mt + P::dy(s) + 8) & (G::NRN - 1)) * G::WRC;
-              acc = fma(sl[G::OFF_Z + s * G::WZ + kz], rrow[c + R + P::dx(s)], acc);
-            }
-            if (edge) {
-              const int col = i0 - R + c;
-              const int cm = col < 0 ? col + nx : (col >= nx ? col - nx : col);
-#pragma unroll
-              for (int w = 0; w < (NW > 0 ? NW : 1); ++w)
-                if (cm == nx - 1 - P::wcol(w)) acc = fma(zwrap[(size_t)mt * NW + w], rnt[c + R + P::wdx(w)], acc);
-            }
-            acc *= sl[G::OFF_DI + kz];
-          }
-          tm[c] = acc;
-        }
-      }
-      // s = Z t on row r = m - 2 - LD
-      const int r = m - 2 - LD;
-      if (r >= j0 && r < rend) {
-        const int col = i0 + tid;
-        if (col < nx) {
-          const T *tr = tt + (size_t)((r + 8) & (G::NTT - 1)) * G::WTC;
-          T acc = tr[tid + R];
-#pragma unroll
-          for (int s = 0; s < NZ; ++s) {
-            const int rowz = r - P::dy(s);           // row of the column holding Z[(col,r), that column]
-            const T *slz = ring + (size_t)(G::slot(rowz - mlo)) * G::SLOT;
-            const T *trow = tt + (size_t)((rowz + 8) & (G::NTT - 1)) * G::WTC;
-            acc = fma(slz[G::OFF_Z + s * G::WZ + tid - P::dx(s) + G::HZ], trow[tid + R - P::dx(s)], acc);
-          }
-          if (edge) {
-#pragma unroll
-            for (int w = 0; w < (NW > 0 ? NW : 1); ++w) {
-              const int target = P::wdx(w) - 1 - P::wcol(w);   // 0 or 1
-              if (col == target) acc = fma(zwrap[(size_t)r * NW + w], tr[tid + R - P::wdx(w)], acc);
-            }
-          }
-          const T *rnr = rn + (size_t)((r + 8) & (G::NRN - 1)) * G::WRC;
-          const T rv = rnr[tid + 2 * R];
-          const size_t ro = (size_t)r * pitch;
-          store_dup(s_out + ro, col, nx, acc);
-          if (kind != K2_APPLY) store_dup(rout + ro, col, nx, rv);
-          dot0.add(acc, rv);
-          dot1.add(rv, rv);
-        }
-      }
-      if (!compute_sync_and<TX>(got)) {
-        if (tid == 0) { ctl[0] = 1; flag_timeout(st); }
-        break;
-      }
-      if (m <= mhi) consumed = m;
-      // row m-2-LD is finished: its slot may be refilled
-      if (tid == 0 && m - 2 - LD >= mlo && m - 2 - LD + G::NST <= mhi) mbar_arrive(&empty[G::slot(m - 2 - LD - mlo)]);
     }
-    if (tid == 0) ctl[2] = consumed;
-    acc0 = dot0.total();
-    acc1 = dot1.total();
+    if (tid == 0) rc.ctl[CTL_SEEN] = (int)seen;
   }
   __syncthreads();
-  if (tid == 0 && ctl[0]) {
-    for (int w = 0; w < G::NPW; ++w)
-      for (int m = mlo + w; m <= ctl[3 + w]; m += G::NPW)
-        if (m > ctl[2])
-          mbar_wait_bounded(&full[G::slot(m - mlo)], (uint32_t)(((m - mlo) / G::NST) & 1), p.timeout_ns);
-  }
-  if (kind == K2_APPLY) return;
-  if (grid_reduce2<NT>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt2, red, flag)) {
-    if (threadIdx.x == 0) {
-      const double rho_new = acc0, rr = acc1;
-      st->rr = rr;
-      st->rsel = rsel ^ 1;
-      if (kind == K2_ITER) {
-        st->beta = rho_new / st->rho;
-        st->pending = st->alpha;
-        st->iter += 1;
-      } else {
-        st->beta = 0.0;
-        st->pending = 0.0;
-      }
-      st->rho = rho_new;
-      const double relres = sqrt(rr) / sqrt(st->bb);
-      if (st->status != PCG_OK) grid_finished(st, ls, PCG_OK, true, p);
-      else if (!isfinite(rho_new) || !isfinite(rr)) grid_finished(st, ls, PCG_EBREAKDOWN, true, p);
-      else if (!(relres > st->rtol)) grid_finished(st, ls, PCG_OK, true, p);
-      else if (st->iter >= st->max_iter) grid_finished(st, ls, PCG_ENOTCONV, true, p);
-      else if (!(rho_new > 0.0)) grid_finished(st, ls, PCG_EBREAKDOWN, true, p);
-    }
-  }
+  drain_groups<G::NSG>(rc, p.timeout_ns);
 }
 
 // ------------------------------------------------------------ small kernels

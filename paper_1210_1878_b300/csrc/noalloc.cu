@@ -75,6 +75,10 @@ extern "C" int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void 
 
   // descriptor: the handle's coefficient planes, the scratch planes for v and q
   GridDev<double> gd = P.gd;
+  // binary64 kernel 1 streams one row per copy straight from the plane
+  // pointers below; tensor maps would name the handle's own planes
+  if (P.ks.rb1 != 1) { set_error("allocation-free operator apply needs one-row streaming"); return PCG_EINVAL; }
+  gd.tm = nullptr;
   gd.d[0] = plane_v + origin;
   gd.d[1] = plane_v + origin;
   gd.q = plane_q + origin;
@@ -96,7 +100,8 @@ extern "C" int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void 
     void *pack_args[] = {&p, (void *)&vin, &which};
     CK(cudaLaunchKernel(P.ks.pack, dim3(P.n_units), dim3(P.tx), pack_args, 0, s));
     void *k_args[] = {&p};
-    CK(cudaLaunchKernel(P.ks.k1, dim3(P.n_units), dim3(P.ks.tb), k_args, P.ks.smem1, s));
+    p.n_units = P.n_units;
+    CK(cudaLaunchKernel(P.ks.k1[K1_SPMV], dim3(persistent_grid(P.ks, 1, P.n_units)), dim3(P.ks.tb), k_args, P.ks.smem1, s));
   }
   const GridDev<double> *gdp = reinterpret_cast<const GridDev<double> *>(b8);
   double *qout = q;
