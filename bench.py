@@ -400,6 +400,70 @@ def run_serve(args, wl_name, wl):
     return 0
 
 
+def _kernel_roofline(pcg, h, b, wl, prec, n_wet, zbar, workload):
+    """Per-kernel roofline, live: mean CUDA-event duration of each of the two
+    kernels of an iteration over 20 launches, against the algorithmic bytes
+    (or binary64 flops) of one launch."""
+    mixed = prec == 1
+    ms_k1, ms_k2 = pcg.pcg_profile_kernels(h, b, iters=20, prec=prec)
+    w = 4 if mixed else 8
+    bytes_k1 = n_wet * w * 9                   # read s, d, x, a, c_e, c_n; write d, x, q
+    bytes_k2 = n_wet * w * (5 + zbar)          # read r, q, Z, D^-1; write r, s
+    flops_k1 = n_wet * 15.0                    # d (1 FMA), x (1 FMA), A d (1 mul + 4 FMA), d.q (1 FMA)
+    flops_k2 = n_wet * (4 * zbar + 7)          # r (1 FMA), Z^T (zbar FMA + 1 mul), Z (zbar FMA), 2 dots
+    fp64_k1 = flops_k1 if not mixed else n_wet * 2.0          # binary32 kernels: only the dots in binary64
+    fp64_k2 = flops_k2 if not mixed else n_wet * 4.0
+    hbm_peak, peak_kind = _peaks()
+    dom = "k_precond" if ms_k2 >= ms_k1 else "k_stencil"
+    ms_dom, by, fl = (ms_k2, bytes_k2, fp64_k2) if dom == "k_precond" else (ms_k1, bytes_k1, fp64_k1)
+    gbs = by / (ms_dom * 1e-3) / 1e9
+    tflops = fl / (ms_dom * 1e-3) / 1e12
+    t_hbm = by / (hbm_peak * 1e9)
+    t_alu = fl / (FP64_PEAK_TFLOPS * 1e12)
+    kname = dom + ("<float>" if mixed else "<double>")
+    traffic = _traffic_record(f"{kname}:{workload}")
+    if t_alu > t_hbm:
+        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_kind": "FP64 FMA pipe derived from 2 FMA/clk/SM x 148 SMs x 2.032 GHz",
+                "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "peak_kind": peak_kind + " (of measured copy bandwidth)" if peak_kind == "measured" else peak_kind}}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": traffic, "peak_kind": peak_kind}
+    it_bytes = bytes_k1 + bytes_k2
+    roof.update({"kernel": kname, "ms_per_launch": ms_dom, "alg_bytes_per_launch": by,
+                 "per_iteration": {"ms_stencil": ms_k1, "ms_precond": ms_k2, "alg_bytes": it_bytes,
+                                   "alg_gbs": it_bytes / ((ms_k1 + ms_k2) * 1e-3) / 1e9,
+                                   "hbm_frac": it_bytes / ((ms_k1 + ms_k2) * 1e-3) / 1e9 / hbm_peak}})
+    return roof
+
+
+def _time_solves(pcg, torch, h, b, x, opts, steps, warmup, stream, barrier, world):
+    for _ in range(warmup):
+        st = pcg.pcg_solve(h, b, x, opts)
+    barrier()
+    torch.cuda.synchronize()
+    l0 = pcg.pcg_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(steps):
+        stats.append(pcg.pcg_solve(h, b, x, opts))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = pcg.pcg_kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    assert all(s.status == pcg.PCG_OK for s in stats), [s.as_dict() for s in stats if s.status]
+    return ms, stats, launches
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,6 +474,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-seconds", type=float, default=8.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="binary64 workloads: skip the mixed-precision companion")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="set up the workload and launch each kernel of an iteration 3 times (for ncu)")
     ap.add_argument("--inner-rtol", type=float, default=0.0)
     ap.add_argument("--tile-x", type=int, default=0)
     ap.add_argument("--tile-y", type=int, default=0)
@@ -448,42 +515,28 @@ def main():
                             tile_y=args.tile_y)
     setup_s = time.perf_counter() - t
     n_wet = h.n_wet
-    zbar = _z_offdiag_per_wet(pcg, h)
-    opts = pcg.make_opts(rtol=wl["rtol"], max_iter=5000, prec=wl["prec"], inner_rtol=args.inner_rtol)
     stream = torch.cuda.current_stream()
     b = torch.from_numpy(grid.b).cuda()
     x = torch.zeros_like(b)
+    if args.kernels_only:
+        print(pcg.pcg_profile_kernels(h, b, iters=3, prec=wl["prec"]))
+        h.close()
+        return 0
+    zbar = _z_offdiag_per_wet(pcg, h)
+    opts = pcg.make_opts(rtol=wl["rtol"], max_iter=5000, prec=wl["prec"], inner_rtol=args.inner_rtol)
 
     for _ in range(args.warmup):
-        st = pcg.pcg_solve(h, b, x, opts)
-    iters = st.iters
-
+        pcg.pcg_solve(h, b, x, opts)
     sampler = ClockSampler(local)
     sampler.start()
     time.sleep(0.3)
-    barrier()
-    torch.cuda.synchronize()
-    l0 = pcg.pcg_kernel_launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    stats = []
-    for _ in range(args.steps):
-        stats.append(pcg.pcg_solve(h, b, x, opts))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    launches = pcg.pcg_kernel_launches() - l0
+    ms, stats, launches = _time_solves(pcg, torch, h, b, x, opts, args.steps, 0, stream, barrier, world)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    st = stats[-1]
+    iters = st.iters
     ms_per_step = ms / args.steps
     value = world * args.steps / (ms / 1e3)
     worst_true = max(s.true_relres for s in stats)
-    assert all(s.status == pcg.PCG_OK for s in stats), [s.as_dict() for s in stats if s.status]
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     bh = torch.from_numpy(grid.b.copy()).pin_memory()
@@ -506,39 +559,22 @@ def main():
     e2e_value = world * args.e2e_steps / (ms_e2e / 1e3)
     vec_bytes = grid.nx * grid.ny * 8
 
-    # per-kernel roofline, live: mean event-timed duration of each kernel launch
-    mixed = wl["prec"] == 1
-    ms_k1, ms_k2 = pcg.pcg_profile_kernels(h, b, iters=20, prec=wl["prec"])
-    w = 4 if mixed else 8
-    bytes_k1 = n_wet * w * 9                   # read s, d, x, a, c_e, c_n; write d, x, q
-    bytes_k2 = n_wet * w * (5 + zbar)          # read r, q, Z, D^-1; write r, s
-    flops_k1 = n_wet * 15.0                    # d (1 FMA), x (1 FMA), A d (1 mul + 4 FMA), d.q (1 FMA)
-    flops_k2 = n_wet * (4 * zbar + 7)          # r (1 FMA), Z^T (zbar FMA + 1 mul), Z (zbar FMA), 2 dots
-    fp64_flops_k1 = flops_k1 if not mixed else n_wet * 2.0          # binary32 kernels: only the dot in binary64
-    fp64_flops_k2 = flops_k2 if not mixed else n_wet * 4.0
-    hbm_peak, peak_kind = _peaks()
-    dom = "k_precond" if ms_k2 >= ms_k1 else "k_stencil"
-    ms_dom, by, fl = (ms_k2, bytes_k2, fp64_flops_k2) if dom == "k_precond" else (ms_k1, bytes_k1, fp64_flops_k1)
-    gbs = by / (ms_dom * 1e-3) / 1e9
-    tflops = fl / (ms_dom * 1e-3) / 1e12
-    t_hbm = by / (hbm_peak * 1e9)
-    t_alu = fl / (FP64_PEAK_TFLOPS * 1e12)
-    key = f"{dom}:{args.workload}"
-    traffic = _traffic_record(key)
-    if t_alu > t_hbm:
-        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
-                "peak_kind": "FP64 FMA pipe derived from 2 FMA/clk/SM x 148 SMs x 2.032 GHz",
-                "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                        "peak_kind": peak_kind}}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                "traffic": traffic, "peak_kind": peak_kind}
-    roof.update({"kernel": dom + ("<float>" if mixed else "<double>"), "ms_per_launch": ms_dom,
-                 "per_iteration": {"ms_stencil": ms_k1, "ms_precond": ms_k2,
-                                   "alg_bytes": bytes_k1 + bytes_k2,
-                                   "alg_gbs": (bytes_k1 + bytes_k2) / ((ms_k1 + ms_k2) * 1e-3) / 1e9,
-                                   "hbm_frac": (bytes_k1 + bytes_k2) / ((ms_k1 + ms_k2) * 1e-3) / 1e9 / hbm_peak}})
+    roof = _kernel_roofline(pcg, h, b, wl, wl["prec"], n_wet, zbar, args.workload)
+
+    # binary64 workloads: the same grid and right-hand side solved in the mixed
+    # precision mode (binary32 inner PCG, binary64 refinement; same acceptance
+    # test: true binary64 relative residual <= rtol)
+    mixed = None
+    if wl["prec"] == 0 and not args.no_mixed:
+        om = pcg.make_opts(rtol=wl["rtol"], max_iter=5000, prec=1, inner_rtol=args.inner_rtol)
+        steps_m = max(3, args.steps // 2)
+        ms_m, stats_m, launches_m = _time_solves(pcg, torch, h, b, x, om, steps_m, args.warmup, stream, barrier,
+                                                 world)
+        mixed = {"value": world * steps_m / (ms_m / 1e3), "unit": UNIT, "ms_per_step": ms_m / steps_m,
+                 "steps": steps_m, "dtype": "f32+f64", "iters_per_solve": stats_m[-1].iters,
+                 "outer_per_solve": stats_m[-1].outer_iters,
+                 "worst_true_relres": max(s.true_relres for s in stats_m), "gpu_launches": int(launches_m),
+                 "roofline": _kernel_roofline(pcg, h, b, wl, 1, n_wet, zbar, args.workload)}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -565,6 +601,8 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
         }
+        if mixed is not None:
+            line["mixed"] = mixed
         print(json.dumps(line))
     h.close()
     if world > 1:

@@ -95,8 +95,8 @@ typedef struct {
   int32_t pattern;     /* pcg_pattern */
   double drop_tol;     /* drop |z_mk| sqrt(a_mm / a_kk) < drop_tol after every update; 0 = keep all */
   int32_t band_q;      /* PCG_PAT_BAND_T only: upper bandwidth q, 1..8 */
-  int32_t tile_x;      /* device strip width in points: 32, 64 or 128; 0 = chosen from nx */
-  int32_t tile_y;      /* device strip height in rows, 4..256; 0 = chosen from ny */
+  int32_t tile_x;      /* device strip width in points: 64 or 128; 0 = chosen per precision from nx */
+  int32_t tile_y;      /* device strip height in rows, 4..256; 0 = chosen per precision from nx, ny */
 } ainv_opts;
 
 typedef enum { PCG_FP64 = 0, PCG_MIXED = 1 } pcg_precision;

@@ -186,7 +186,8 @@ static int upload_planes(pcg_handle *h, DevPlanes<T> &P, cudaStream_t s) {
   const HostGrid &G = h->G;
   const HostFactor &F = h->F;
   P.nx = G.nx; P.ny = G.ny;
-  P.tx = h->tx; P.ty = h->ty;
+  P.tx = sizeof(T) == 4 ? h->tx32 : h->tx;
+  P.ty = sizeof(T) == 4 ? h->ty32 : h->ty;
   P.gx = 128 / (int)sizeof(T);
   const int ntx = (G.nx + P.tx - 1) / P.tx;
   P.pitch = (int)elem_round((size_t)P.gx + (size_t)ntx * P.tx + P.gx, 128 / sizeof(T));
@@ -847,16 +848,20 @@ std::string status_name(int s) {
   }
 }
 
-static int choose_tx(int nx) {
-  // the strip width that wastes the fewest columns; ties go to the wider strip
+// Strip width. binary64 kernels are bound by the FP64 pipe: narrow strips,
+// more CTAs per SM. binary32 kernels: the width that wastes the fewest
+// columns, ties to the wider strip (fewer halo columns per point).
+static int choose_tx(int nx, int elem_size) {
+  if (elem_size == 8) return 64;
   const int w128 = (nx + 127) / 128 * 128, w64 = (nx + 63) / 64 * 64;
   return (w128 - nx <= (w64 - nx) + 16) ? 128 : 64;
 }
 
+// Strip height: about 600 units when the grid allows (the persistent CTAs
+// then take one to a few units each), a multiple of 8 rows in 8..64.
 static int choose_ty(int nx, int ny, int tx) {
   const int ntx = (nx + tx - 1) / tx;
-  // aim at >= ~4 CTAs per SM of 148 when the grid allows it, rows 8..32
-  int ty = (int)std::floor((double)ntx * ny / (148.0 * 4));
+  const int ty = (int)((double)ntx * ny / 600.0) / 8 * 8;
   return std::max(8, std::min(64, ty));
 }
 
@@ -946,10 +951,12 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     h->pattern = opts->pattern;
     h->band_q = opts->band_q;
     h->tau = opts->drop_tol;
-    h->tx = opts->tile_x ? opts->tile_x : choose_tx(grid->nx);
-    if (h->tx != 64 && h->tx != 128) { set_error("tile_x must be 64 or 128"); return PCG_EINVAL; }
+    if (opts->tile_x != 0 && opts->tile_x != 64 && opts->tile_x != 128) { set_error("tile_x must be 64 or 128"); return PCG_EINVAL; }
+    if (opts->tile_y != 0 && (opts->tile_y < 4 || opts->tile_y > 256)) { set_error("tile_y must be 4..256"); return PCG_EINVAL; }
+    h->tx = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 8);
     h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx);
-    if (h->ty < 4 || h->ty > 256) { set_error("tile_y must be 4..256"); return PCG_EINVAL; }
+    h->tx32 = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 4);
+    h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     rc = upload_planes(h.get(), h->p64, s);
     if (rc) { h->p64.release(); return rc; }

@@ -101,7 +101,8 @@ struct pcg_handle {
   pcg::HostFactor F;
   int pattern = 0, band_q = 0;
   double tau = 0.0;
-  int tx = 0, ty = 0;
+  int tx = 0, ty = 0;                     // strips of the binary64 planes
+  int tx32 = 0, ty32 = 0;                 // strips of the binary32 planes
   pcg::DevPlanes<double> p64;
   pcg::DevPlanes<float> p32;              // binary32 copies for the mixed-precision inner solves (lazy)
   pcg::SolveState *st32_host = nullptr;   // pinned mirror of p32's state
