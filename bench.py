@@ -347,6 +347,7 @@ def run_serve(args, wl_name, wl):
     steps_done = [0] * len(grids)
     ids = []
     late = []
+    call_ms = []      # client-side time of the right-hand-side update and of the submit call
     sampler = _sample_clocks(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.perf_counter()
     for t_arr, k in zip(arrivals, grid_pick):
@@ -355,10 +356,14 @@ def run_serve(args, wl_name, wl):
             time.sleep(t_arr - now)
         else:
             late.append(now - t_arr)
+        ta = time.perf_counter()
         cur[k].add_(noise[k][steps_done[k] % 2])
         steps_done[k] += 1
+        tb = time.perf_counter()
         rid = srv.submit(gids[k], cur[k], outs[k], warm_start=True)
-        ids.append((t_arr, k, rid, time.perf_counter() - t0))
+        tc = time.perf_counter()
+        call_ms.append(((tb - ta) * 1e3, (tc - tb) * 1e3))
+        ids.append((t_arr, k, rid, tc - t0))
     results = []
     for t_arr, k, rid, t_sub in ids:
         rc, st = srv.wait(rid, timeout_ms=600000)
@@ -388,6 +393,9 @@ def run_serve(args, wl_name, wl):
         "dtype": "f32+f64" if wl["prec"] == 1 else "f64", "data": "synthetic",
         "config": {"workload": wl_name, "arrival_rate_per_s": wl["rate"], "seconds": seconds, "warm_s": warm_s,
                    "submit_late_p99_ms": (float(np.percentile(late, 99)) * 1e3) if late else 0.0,
+                   "client_update_ms_p99": float(np.percentile([c[0] for c in call_ms], 99)) if call_ms else 0.0,
+                   "client_submit_ms_p99": float(np.percentile([c[1] for c in call_ms], 99)) if call_ms else 0.0,
+                   "client_submit_ms_max": float(max(c[1] for c in call_ms)) if call_ms else 0.0,
                    "requests": len(results), "failed": len(results) - sum(1 for r in results if r[2] == 0),
                    "grids": {f"{c['nx']}x{c['ny']}": n for c, n in pool}, "hbm_budget_gb": 150,
                    "max_slots": 16, "chunk_iters": args.chunk,

@@ -107,7 +107,9 @@ typedef struct {
   int32_t prec;        /* pcg_precision. PCG_MIXED: binary32 inner PCG inside a binary64
                           iterative-refinement loop (binary64 outer residual, x update and
                           inner dot-product accumulation) */
-  double inner_rtol;   /* PCG_MIXED: relative tolerance of each inner solve (default 1e-5 if <= 0) */
+  double inner_rtol;   /* PCG_MIXED: relative tolerance of an inner solve (default 1e-5 if <= 0); once the
+                          reduction still needed, rtol / relres, is >= inner_rtol / 10, the inner solve asks
+                          for half of it instead (floor inner_rtol / 10) */
   int32_t max_outer;   /* PCG_MIXED: cap on refinement steps (default 30 if <= 0) */
   int32_t use_x0;      /* nonzero: x holds the initial guess on entry; zero: start from x = 0 */
   int32_t max_replace; /* FP64: restarts from the true residual when it fails rtol on exit (default 3 if < 0) */
@@ -199,6 +201,17 @@ int ainv_factor_host(const pcg_grid *grid, const ainv_opts *opts, int32_t *n_wet
  * call returns that recorded status (PCG_ETIMEOUT when the guard works). The
  * handle stays usable. No GPU fault is involved. */
 int pcg_debug_wait_timeout(pcg_handle *h, int32_t unit, double timeout_ms, void *cuda_stream);
+
+/* The binary32 kernels of the mixed-precision mode (the inner iterations of
+ * the refinement loop) on one operand, for checking them alone:
+ *   op 0: out = A v (Section 3, Eq. 9 in SPD form), the stencil kernel;
+ *   op 1: out = Z D^-1 Z^T v (the preconditioning step of Algorithm 1), the
+ *         preconditioner kernel.
+ * v and out are [ny][nx] binary64 (host or device); v is rounded to binary32
+ * on the way in, the binary32 result widened on the way out; land entries of
+ * out are 0. Builds the handle's binary32 planes on first use. Returns PCG_OK,
+ * PCG_EINVAL (NULL argument or op not 0/1), PCG_ENOMEM or PCG_ECUDA. */
+int pcg_apply_f32(pcg_handle *h, int32_t op, const double *v, double *out, void *cuda_stream);
 
 /* Measurement entry point: loads b, runs the init kernels, then `iters` PCG
  * iterations as individual launches of the stencil kernel and of the

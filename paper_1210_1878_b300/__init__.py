@@ -26,6 +26,7 @@ PCG_FP64, PCG_MIXED = 0, 1
 
 EXPORTED = [
     "ainv_setup", "ainv_factor_host", "pcg_solve", "pcg_solve_batched", "pcg_spmv", "pcg_spmv_noalloc", "pcg_precond_apply",
+    "pcg_apply_f32",
     "pcg_ainv_export", "pcg_resident_bytes", "pcg_n_wet", "pcg_free", "pcg_status_string",
     "pcg_last_error_message", "pcg_debug_wait_timeout", "pcg_profile_kernels", "pcg_kernel_launches", "solver_server_create", "solver_server_register", "solver_server_submit",
     "solver_server_wait", "solver_server_cancel", "solver_server_stats", "solver_server_destroy",
@@ -89,6 +90,7 @@ def _load():
         "pcg_spmv": (C.c_int, [vp, vp, vp, vp]),
         "pcg_spmv_noalloc": (C.c_int, [vp, vp, vp, vp]),
         "pcg_precond_apply": (C.c_int, [vp, vp, vp, vp]),
+        "pcg_apply_f32": (C.c_int, [vp, i32, vp, vp, vp]),
         "pcg_ainv_export": (C.c_int, [vp, C.POINTER(i32), vp, vp, vp]),
         "pcg_resident_bytes": (C.c_size_t, [vp]),
         "pcg_n_wet": (i32, [vp]),
@@ -265,6 +267,13 @@ def pcg_precond_apply(h: Handle, r, s, stream=None):
     rc = lib.pcg_precond_apply(h.ptr, _ptr(r), _ptr(s), _stream(stream))
     if rc != PCG_OK:
         raise PCGError(rc, "pcg_precond_apply")
+
+
+def pcg_apply_f32(h: Handle, op: int, v, out, stream=None):
+    """The binary32 kernels on one operand: op 0 out = A v, op 1 out = M^-1 v."""
+    rc = lib.pcg_apply_f32(h.ptr, int(op), _ptr(v), _ptr(out), _stream(stream))
+    if rc != PCG_OK:
+        raise PCGError(rc, "pcg_apply_f32")
 
 
 def pcg_ainv_export(h: Handle):

@@ -420,8 +420,8 @@ bool is_device_ptr(const void *p) {
 }
 
 // Pack a user [ny][nx] binary64 vector into plane `which` (0 b, 1 x, 2 r0, 3 d0).
-static int pack_user(pcg_handle *h, const double *user, int which, cudaStream_t s) {
-  auto &P = h->p64;
+template <typename T>
+static int pack_user(pcg_handle *h, DevPlanes<T> &P, const double *user, int which, cudaStream_t s) {
   const double *srcp = user;
   if (!is_device_ptr(user)) {
     CK(cudaMemcpyAsync(h->stage, user, sizeof(double) * (size_t)P.nx * P.ny, cudaMemcpyHostToDevice, s));
@@ -437,11 +437,11 @@ static int pack_user(pcg_handle *h, const double *user, int which, cudaStream_t 
 }
 
 // Unpack plane `which` (0 x, 1 s, 2 q) into a user [ny][nx] binary64 vector.
-static int unpack_user(pcg_handle *h, double *user, int which, cudaStream_t s) {
-  auto &P = h->p64;
+template <typename T>
+static int unpack_user(pcg_handle *h, DevPlanes<T> &P, double *user, int which, cudaStream_t s) {
   const bool dev = is_device_ptr(user);
   double *dst = dev ? user : h->stage;
-  const GridDev<double> *gdp = P.gd_dev;
+  const GridDev<T> *gdp = P.gd_dev;
   void *args[] = {(void *)&gdp, (void *)&dst, &which};
   const size_t n = (size_t)P.nx * P.ny;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
@@ -558,9 +558,9 @@ int member_load(Member &m, const pcg_opts &o, bool pack_x0, cudaStream_t s) {
   auto &P = m.h->p64;
   int rc;
   const int max_iter = o.max_iter > 0 ? o.max_iter : std::max(m.h->G.n, 1);
-  if ((rc = pack_user(m.h, m.b, 0, s))) return rc;
+  if ((rc = pack_user(m.h, m.h->p64, m.b, 0, s))) return rc;
   if (o.use_x0) {
-    if (pack_x0 && (rc = pack_user(m.h, m.x, 1, s))) return rc;
+    if (pack_x0 && (rc = pack_user(m.h, m.h->p64, m.x, 1, s))) return rc;
   } else {
     CK(cudaMemsetAsync(P.plane_start(P.vec(0)), 0, P.plane_elems * sizeof(double), s));
   }
@@ -626,7 +626,7 @@ bool member_decide(Member &m, const pcg_opts &o, bool overrun, cudaStream_t s, i
   return true;
 }
 
-int member_store(Member &m, cudaStream_t s) { return unpack_user(m.h, m.x, 0, s); }
+int member_store(Member &m, cudaStream_t s) { return unpack_user(m.h, m.h->p64, m.x, 0, s); }
 
 void member_stats(Member &m) {
   SolveState &st = *m.st_host;
@@ -724,7 +724,13 @@ bool mixed_prepare_inner(Member &m, const pcg_opts &o, int budget, int outer, cu
     if (cudaMemsetAsync(P32.plane_start(P32.vec(0)), 0, P32.plane_elems * sizeof(float), s) != cudaSuccess) *err = PCG_ECUDA;
     for (int v : {5, 6})
       if (cudaMemsetAsync(P32.plane_start(P32.vec(v)), 0, P32.plane_elems * sizeof(float), s) != cudaSuccess) *err = PCG_ECUDA;
-    st32.rtol = o.inner_rtol;
+    // Inner tolerance. Far from the finish: o.inner_rtol (the binary32 solve
+    // cannot go much below ~1e-6 relative). Within a decade of the finish
+    // (the reduction still needed, rtol / relres, is at least inner_rtol / 10):
+    // half the needed reduction, so that binary32 rounding in the correction
+    // does not leave the solve just above rtol and cost a whole extra pass.
+    const double need = o.rtol / m.relres64;
+    st32.rtol = need >= 0.1 * o.inner_rtol ? std::max(0.5 * need, 0.1 * o.inner_rtol) : o.inner_rtol;
     st32.max_iter = std::max(1, budget - m.inner_iters);
   }
   *m.h->st32_host = st32;
@@ -1042,12 +1048,12 @@ int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream) {
   cudaStream_t s = (cudaStream_t)cuda_stream;
   auto &P = h->p64;
   int rc;
-  if ((rc = pack_user(h, v, 3, s))) return rc;
+  if ((rc = pack_user(h, h->p64, v, 3, s))) return rc;
   KParams p{};
   p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K1_SPMV; p.dbg_skip_unit = -1;
   p.timeout_ns = default_timeout_ns();
   if ((rc = launch_k(P.ks, 1, P.n_units, p, s))) return rc;
-  if ((rc = unpack_user(h, q, 2, s))) return rc;
+  if ((rc = unpack_user(h, h->p64, q, 2, s))) return rc;
   CK(cudaStreamSynchronize(s));
   return PCG_OK;
 }
@@ -1057,12 +1063,30 @@ int pcg_precond_apply(pcg_handle *h, const double *r, double *sv, void *cuda_str
   cudaStream_t s = (cudaStream_t)cuda_stream;
   auto &P = h->p64;
   int rc;
-  if ((rc = pack_user(h, r, 2, s))) return rc;
+  if ((rc = pack_user(h, h->p64, r, 2, s))) return rc;
   KParams p{};
   p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K2_APPLY; p.dbg_skip_unit = -1;
   p.timeout_ns = default_timeout_ns();
   if ((rc = launch_k(P.ks, 2, P.n_units, p, s))) return rc;
-  if ((rc = unpack_user(h, sv, 1, s))) return rc;
+  if ((rc = unpack_user(h, h->p64, sv, 1, s))) return rc;
+  CK(cudaStreamSynchronize(s));
+  return PCG_OK;
+}
+
+int pcg_apply_f32(pcg_handle *h, int32_t op, const double *v, double *out, void *cuda_stream) {
+  if (!h || !v || !out || (op != 0 && op != 1)) { set_error("invalid arguments"); return PCG_EINVAL; }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int rc;
+  if ((rc = ensure_f32(h, s))) return rc;
+  auto &P = h->p32;
+  // op 0: v into d[0], q = A v; op 1: v into r[0], s = M^-1 v
+  if ((rc = pack_user(h, P, v, op == 0 ? 3 : 2, s))) return rc;
+  KParams p{};
+  p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = op == 0 ? (int)K1_SPMV : (int)K2_APPLY;
+  p.dbg_skip_unit = -1;
+  p.timeout_ns = default_timeout_ns();
+  if ((rc = launch_k(P.ks, op == 0 ? 1 : 2, P.n_units, p, s))) return rc;
+  if ((rc = unpack_user(h, P, out, op == 0 ? 2 : 1, s))) return rc;
   CK(cudaStreamSynchronize(s));
   return PCG_OK;
 }

@@ -283,6 +283,7 @@ enum { CTL_ABORT = 0, CTL_ARMED = 1, CTL_SEEN = 2, CTL_FLAG = 3 };
 struct FieldCopy {
   const char *src;      // RB = 1: element (first box column, row 0) of the plane, as bytes
   const void *tmap;     // RB > 1: tensor map of the plane with this field's box
+  int64_t pitch_b;      // RB = 1: bytes between rows of the plane
   int32_t x;            // RB > 1: first box column, counted from the plane's first stored column
   uint32_t dst;         // byte offset of the field in a group slot
   uint32_t bytes;       // bytes of the field in one group
@@ -337,40 +338,49 @@ __device__ __forceinline__ void compute_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory");
 }
 
-// Stream the ng groups of one unit (first rows mlo, mlo + RB, ...). gq is the
-// CTA's running group count; new_grid: the unit's grid differs from the
-// previous unit's (its tensor maps are acquired). Returns false once the CTA
-// is aborting.
-template <int NSG, int RB>
-__device__ __forceinline__ bool produce_unit(const FieldCopy &c, bool has, unsigned char *ring, int group_bytes,
-                                             uint64_t *full, uint64_t *empty, int mlo, int ng, uint32_t &gq,
-                                             size_t pitch_b, bool skip_first, bool new_grid, uint64_t timeout_ns,
-                                             volatile int *ctl) {
+// The producer warp's loop: lane f issues the copies of field f of every
+// group of the CTA's units, in order. setup(ui, f, c, has, mlo, ng) describes
+// unit ui's field f (returns false for a unit to skip). Returns the number of
+// groups armed; stops early once the CTA is aborting.
+template <int NSG, int RB, class Setup>
+__device__ __forceinline__ uint32_t produce_all(const KParams &p, unsigned char *ring, int group_bytes, uint64_t *full,
+                                                uint64_t *empty, volatile int *ctl, Setup setup) {
   const int lane = threadIdx.x & 31;
-  if constexpr (RB > 1)
-    if (has && new_grid) tensormap_acquire(c.tmap);
-  const uint32_t total = __reduce_add_sync(0xffffffffu, has ? c.bytes : 0u);
-  for (int q = 0; q < ng; ++q, ++gq) {
-    const uint32_t slot = gq % NSG, fill = gq / NSG;
-    if (fill > 0) {
-      bool ok = true;
-      if (lane == 0) ok = mbar_wait_or_abort(&empty[slot], (fill - 1) & 1u, timeout_ns, &ctl[CTL_ABORT]);
-      if (!__shfl_sync(0xffffffffu, ok, 0)) {
-        if (lane == 0) ctl[CTL_ABORT] = 1;
-        return false;
+  uint32_t gq = 0;
+  int last_g = -1;
+  for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
+    FieldCopy c{};
+    bool has = false;
+    int mlo = 0, ng = 0;
+    if (!setup(ui, lane, c, has, mlo, ng)) continue;
+    const int g_un = p.units[ui].g;
+    const bool skip_first = (p.dbg_skip_unit == ui) && lane == 0;
+    if constexpr (RB > 1)
+      if (has && g_un != last_g) tensormap_acquire(c.tmap);
+    last_g = g_un;
+    const uint32_t total = __reduce_add_sync(0xffffffffu, has ? c.bytes : 0u);
+    for (int q = 0; q < ng; ++q, ++gq) {
+      const uint32_t slot = gq % NSG, fill = gq / NSG;
+      if (fill > 0) {
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait_or_abort(&empty[slot], (fill - 1) & 1u, p.timeout_ns, &ctl[CTL_ABORT]);
+        if (!__shfl_sync(0xffffffffu, ok, 0)) {
+          if (lane == 0) ctl[CTL_ABORT] = 1;
+          return gq;
+        }
+      }
+      if (lane == 0) mbar_arrive_expect_tx(&full[slot], total);
+      __syncwarp();
+      if (has && !(skip_first && q == 0)) {
+        fence_proxy_async();
+        unsigned char *dst = ring + (size_t)slot * group_bytes + c.dst;
+        const int m0 = mlo + q * RB;
+        if constexpr (RB == 1) bulk_g2s(dst, c.src + (ptrdiff_t)m0 * c.pitch_b, c.bytes, &full[slot]);
+        else tma_2d_g2s(dst, c.tmap, c.x, m0 + GY, &full[slot]);
       }
     }
-    if (lane == 0) mbar_arrive_expect_tx(&full[slot], total);
-    __syncwarp();
-    if (has && !(skip_first && q == 0)) {
-      fence_proxy_async();
-      unsigned char *dst = ring + (size_t)slot * group_bytes + c.dst;
-      const int m0 = mlo + q * RB;
-      if constexpr (RB == 1) bulk_g2s(dst, c.src + (ptrdiff_t)m0 * (ptrdiff_t)pitch_b, c.bytes, &full[slot]);
-      else tma_2d_g2s(dst, c.tmap, c.x, m0 + GY, &full[slot]);
-    }
   }
-  return true;
+  return gq;
 }
 
 // Shared-memory geometry common to both kernels: barriers and control words
@@ -686,49 +696,42 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
 
   if (tid >= TX) {
     // ---- producer warp
-    const int lane = tid - TX;
-    uint32_t gq = 0;
-    int last_g = -1;
-    for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
+    auto setup = [&](int ui, int f, FieldCopy &c, bool &has, int &mlo, int &ng) -> bool {
       const Unit un = p.units[ui];
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
-      if (skip_unit(gdp->st)) continue;
+      if (skip_unit(gdp->st)) return false;
       const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
-      const int mlo = j0 - 1, mhi = min(j0 + gdp->ty, gdp->ny);
-      const int ng = (mhi - mlo + G::RB) / G::RB;
+      const int mhi = min(j0 + gdp->ty, gdp->ny);
+      mlo = j0 - 1;
+      ng = (mhi - mlo + G::RB) / G::RB;
       const int dsel = gdp->st->dsel;
       const T *src_s = (kind == K1_ITER) ? gdp->s : (kind == K1_SPMV) ? gdp->d[0] : gdp->x;
       const int tm_s = (kind == K1_ITER) ? TM_WS_S : (kind == K1_SPMV) ? TM_WS_D0 : TM_WS_X;
-      const TensorMapBytes *tm = reinterpret_cast<const TensorMapBytes *>(gdp->tm);
-      const int gx = 128 / (int)sizeof(T);
+      const TensorMapBytes *tm = gdp->tm;
       auto mk = [&](const T *plane, int tmi, int col, int off, int w) {
-        FieldCopy c;
         c.src = reinterpret_cast<const char *>(plane + i0 + col);
         c.tmap = tm ? (const void *)(tm + tmi) : nullptr;
-        c.x = gx + i0 + col;
+        c.pitch_b = (int64_t)gdp->pitch * (int64_t)sizeof(T);
+        c.x = 128 / (int)sizeof(T) + i0 + col;
         c.dst = (uint32_t)off;
         c.bytes = (uint32_t)(G::RB * w * (int)sizeof(T));
-        return c;
       };
-      FieldCopy c{};
-      bool has = true;
-      switch (lane) {
-        case 0: c = mk(src_s, tm_s, -G::H, G::OFF_S, G::WS); break;
-        case 1: c = mk(gdp->d[dsel], dsel ? TM_WS_D1 : TM_WS_D0, -G::H, G::OFF_D, G::WS); has = kind == K1_ITER; break;
-        case 2: c = mk(gdp->cn, TM_WT_CN, 0, G::OFF_N, G::WT); break;
-        case 3: c = mk(gdp->ce, TM_WE_CE, -G::H, G::OFF_E, G::WE); break;
-        case 4: c = mk(gdp->a, TM_WT_A, 0, G::OFF_A, G::WT); break;
-        case 5: c = mk(kind == K1_ITER ? gdp->x : gdp->b, kind == K1_ITER ? TM_WT_X : TM_WT_B, 0, G::OFF_X, G::WT);
+      has = true;
+      switch (f) {
+        case 0: mk(src_s, tm_s, -G::H, G::OFF_S, G::WS); break;
+        case 1: mk(gdp->d[dsel], dsel ? TM_WS_D1 : TM_WS_D0, -G::H, G::OFF_D, G::WS); has = kind == K1_ITER; break;
+        case 2: mk(gdp->cn, TM_WT_CN, 0, G::OFF_N, G::WT); break;
+        case 3: mk(gdp->ce, TM_WE_CE, -G::H, G::OFF_E, G::WE); break;
+        case 4: mk(gdp->a, TM_WT_A, 0, G::OFF_A, G::WT); break;
+        case 5: mk(kind == K1_ITER ? gdp->x : gdp->b, kind == K1_ITER ? TM_WT_X : TM_WT_B, 0, G::OFF_X, G::WT);
                 has = kind != K1_SPMV; break;
         default: has = false; break;
       }
-      const bool skip_first = (p.dbg_skip_unit == ui) && lane == 0;
-      if (!produce_unit<G::NSG, G::RB>(c, has, rc.ring, G::GROUP, rc.full, rc.empty, mlo, ng, gq,
-                                       (size_t)gdp->pitch * sizeof(T), skip_first, un.g != last_g, p.timeout_ns, rc.ctl))
-        break;
-      last_g = un.g;
-    }
-    if (lane == 0) rc.ctl[CTL_ARMED] = (int)gq;
+      return true;
+    };
+    const uint32_t gq =
+        produce_all<G::NSG, G::RB>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, setup);
+    if (tid == TX) rc.ctl[CTL_ARMED] = (int)gq;
   } else {
     // ---- compute threads
     uint32_t gbase = 0, seen = 0;
@@ -1024,43 +1027,36 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
 
   if (tid >= TX) {
     // ---- producer warp
-    const int lane = tid - TX;
-    uint32_t gq = 0;
-    int last_g = -1;
-    for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
+    auto setup = [&](int ui, int f, FieldCopy &c, bool &has, int &mlo, int &ng) -> bool {
       const Unit un = p.units[ui];
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
-      if (skip_unit(gdp->st)) continue;
+      if (skip_unit(gdp->st)) return false;
       const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
       const int rend = min(j0 + gdp->ty, gdp->ny);
-      const int mlo = j0 - LD, mhi = rend + LD - 1;
-      const int ng = (mhi - mlo + G::RB) / G::RB;
+      const int mhi = rend + LD - 1;
+      mlo = j0 - LD;
+      ng = (mhi - mlo + G::RB) / G::RB;
       const int rsel = (kind == K2_APPLY) ? 0 : gdp->st->rsel;
-      const TensorMapBytes *tm = reinterpret_cast<const TensorMapBytes *>(gdp->tm);
-      const int gx = 128 / (int)sizeof(T);
+      const TensorMapBytes *tm = gdp->tm;
       auto mk = [&](const T *plane, int tmi, int col, int off, int w) {
-        FieldCopy c;
         c.src = reinterpret_cast<const char *>(plane + i0 + col);
         c.tmap = tm ? (const void *)(tm + tmi) : nullptr;
-        c.x = gx + i0 + col;
+        c.pitch_b = (int64_t)gdp->pitch * (int64_t)sizeof(T);
+        c.x = 128 / (int)sizeof(T) + i0 + col;
         c.dst = (uint32_t)off;
         c.bytes = (uint32_t)(G::RB * w * (int)sizeof(T));
-        return c;
       };
-      FieldCopy c{};
-      bool has = true;
-      if (lane == 0) c = mk(gdp->r[rsel], rsel ? TM_WR_R1 : TM_WR_R0, -G::HR, G::OFF_R, G::WR);
-      else if (lane == 1) { c = mk(gdp->q, TM_WR_Q, -G::HR, G::OFF_Q, G::WR); has = kind == K2_ITER; }
-      else if (lane - 2 < NZ) c = mk(gdp->z[lane - 2], TM_WZ_Z0 + lane - 2, -G::HZ, G::OFF_Z + (lane - 2) * G::fb(G::WZ), G::WZ);
-      else if (lane - 2 == NZ) c = mk(gdp->dinv, TM_WZ_DI, -G::HZ, G::OFF_DI, G::WZ);
+      has = true;
+      if (f == 0) mk(gdp->r[rsel], rsel ? TM_WR_R1 : TM_WR_R0, -G::HR, G::OFF_R, G::WR);
+      else if (f == 1) { mk(gdp->q, TM_WR_Q, -G::HR, G::OFF_Q, G::WR); has = kind == K2_ITER; }
+      else if (f - 2 < NZ) mk(gdp->z[f - 2], TM_WZ_Z0 + f - 2, -G::HZ, G::OFF_Z + (f - 2) * G::fb(G::WZ), G::WZ);
+      else if (f - 2 == NZ) mk(gdp->dinv, TM_WZ_DI, -G::HZ, G::OFF_DI, G::WZ);
       else has = false;
-      const bool skip_first = (p.dbg_skip_unit == ui) && lane == 0;
-      if (!produce_unit<G::NSG, G::RB>(c, has, rc.ring, G::GROUP, rc.full, rc.empty, mlo, ng, gq,
-                                       (size_t)gdp->pitch * sizeof(T), skip_first, un.g != last_g, p.timeout_ns, rc.ctl))
-        break;
-      last_g = un.g;
-    }
-    if (lane == 0) rc.ctl[CTL_ARMED] = (int)gq;
+      return true;
+    };
+    const uint32_t gq =
+        produce_all<G::NSG, G::RB>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, setup);
+    if (tid == TX) rc.ctl[CTL_ARMED] = (int)gq;
   } else {
     // ---- compute threads
     uint32_t gbase = 0, seen = 0;
