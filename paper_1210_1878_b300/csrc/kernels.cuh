@@ -492,7 +492,10 @@ struct K1Geom {
   // kept small (about 40 KB) for CTAs per SM.
   static constexpr int LIVE = (3 + RB - 1) / RB + 1;
   static constexpr int NSG = RB == 1 ? 8 : ring_groups(40000, GROUP, LIVE);
-  static constexpr int NT = TX + 32;                 // compute threads + the producer warp
+  // NGRP warp groups of TX compute threads (with 2, each step's work is split:
+  // group 0 d', the x update and the waits, group 1 q = A d' and its stores;
+  // measured no faster than 1 on this GPU), then the producer warp
+  static constexpr int NGRP = 1, NC = NGRP * TX, NT = NC + 32;
   static constexpr size_t SMEM = 128 + 256 + (size_t)NSG * GROUP + sizeof(T) * (size_t)NDN * WDN + 16 * (NT / 32) + 64;
 };
 
@@ -549,14 +552,14 @@ struct K1Unit {
   T *d_out, *x_out, *q_out, *r_out;
   uint64_t timeout_ns;
   uint32_t fslot, fpar, eslot;
-  int tid, mlo, nr1, nrows, pitch, ng, nseen, nrel;
+  int tid, lt, grp, mlo, nr1, nrows, pitch, ng, nseen, nrel;   // lt: column in the strip, grp: warp group
   bool col_ok;
   ColStore<T> cs;
   T beta, pend;
   DotAcc<T> dot0, dot1;
 
   __device__ __forceinline__ void begin(const unsigned char *ring, uint32_t gbase) {
-    ring_lo = ring + tid * ESZ;
+    ring_lo = ring + lt * ESZ;
     ring_hi = ring_lo + (size_t)NSG * G::GROUP;
     fslot = gbase % NSG;
     fpar = (gbase / NSG) & 1u;
@@ -582,10 +585,12 @@ struct K1Unit {
       next_sb += G::GROUP;
       if (next_sb == ring_hi) next_sb = ring_lo;
     }
+    const bool ga = G::NGRP == 1 || grp == 0, gb1 = G::NGRP == 1 || grp == 1;
     // Loads of a step come before its shared-memory stores: q on row m - 2
     // first (it reads d' rows written in earlier steps), then d' on row m.
     // q = A d' on row r = m - 2 (rel - 3 = r - j0)
-    if (rel >= 3 && rel - 3 < nrows && col_ok) {
+    const bool qrow = rel >= 3 && rel - 3 < nrows && col_ok;
+    if (gb1 && qrow) {
       const unsigned char *br = gb[gback(K, 2)], *bs = gb[gback(K, 3)];
       constexpr int IR = pmod(K - 2, RB), IS = pmod(K - 3, RB);
       const T *dr = dn + pmod(K - 2, G::NDN) * G::WDN;
@@ -602,9 +607,8 @@ struct K1Unit {
       av = fma(-Nr[0], dnn[1], av);
       const size_t ro = (size_t)(mlo + rel - 2) * pitch;
       if (kind == K1_ITER) {
-        const T xv = fma(pend, Dr[G::H], Xr[0]);
         cs.put(d_out + ro, c_ctr);
-        cs.put(x_out + ro, xv);
+        if constexpr (G::NGRP == 1) cs.put(x_out + ro, fma(pend, Dr[G::H], Xr[0]));
         cs.put(q_out + ro, av);
         dot0.add(c_ctr, av);
       } else if (kind == K1_SPMV) {
@@ -617,9 +621,18 @@ struct K1Unit {
         dot1.add(bv, bv);
       }
     }
+    if constexpr (G::NGRP == 2 && KIND == K1_ITER) {
+      // x += pending d_old on row r (group 0)
+      if (grp == 0 && qrow) {
+        const unsigned char *br = gb[gback(K, 2)];
+        constexpr int IR = pmod(K - 2, RB);
+        const T *Xr = fld<G::OFF_X>(br, IR, G::WT), *Dr = fld<G::OFF_D>(br, IR, G::WS);
+        cs.put(x_out + (size_t)(mlo + rel - 2) * pitch, fma(pend, Dr[G::H], Xr[0]));
+      }
+    }
     // last: d' on row m (the only part that waits for streamed data)
     bool got = true, waited = false;
-    if (rel <= nr1) {                                  // row m = mlo + rel is streamed
+    if (ga && rel <= nr1) {                            // row m = mlo + rel is streamed
       if constexpr (I == 0) {
         got = mbar_wait_or_abort(&full[fslot], fpar, timeout_ns, abort);
         waited = true;
@@ -631,13 +644,13 @@ struct K1Unit {
       T v = S[G::H - 1];
       if (kind == K1_ITER) v = fma(beta, D[G::H - 1], v);
       dnm[0] = v;
-      if (tid < G::WDN - TX) {
+      if (lt < G::WDN - TX) {
         T v2 = S[G::H - 1 + TX];
         if (kind == K1_ITER) v2 = fma(beta, D[G::H - 1 + TX], v2);
         dnm[TX] = v2;
       }
     }
-    if (!compute_sync_and<TX>(got)) return false;
+    if (!compute_sync_and<G::NC>(got)) return false;
     if (waited) ++nseen;
     // row m - 3 is finished: at the last row of its group, release the group
     if constexpr (pmod(K - 2, RB) == 0) {
@@ -694,7 +707,7 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
     return false;
   };
 
-  if (tid >= TX) {
+  if (tid >= G::NC) {
     // ---- producer warp
     auto setup = [&](int ui, int f, FieldCopy &c, bool &has, int &mlo, int &ng) -> bool {
       const Unit un = p.units[ui];
@@ -731,7 +744,7 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
     };
     const uint32_t gq =
         produce_all<G::NSG, G::RB>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, setup);
-    if (tid == TX) rc.ctl[CTL_ARMED] = (int)gq;
+    if (tid == G::NC) rc.ctl[CTL_ARMED] = (int)gq;
   } else {
     // ---- compute threads
     uint32_t gbase = 0, seen = 0;
@@ -749,13 +762,14 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
       double acc0 = 0.0, acc1 = 0.0;
       if (!aborted) {
         K1Unit<T, TX, KIND> cx;
-        cx.tid = tid; cx.dn = dn + tid; cx.full = rc.full; cx.empty = rc.empty; cx.abort = &rc.ctl[CTL_ABORT];
+        cx.tid = tid; cx.grp = tid / TX; cx.lt = tid - cx.grp * TX;
+        cx.dn = dn + cx.lt; cx.full = rc.full; cx.empty = rc.empty; cx.abort = &rc.ctl[CTL_ABORT];
         cx.timeout_ns = p.timeout_ns;
         cx.begin(rc.ring, gbase);
         cx.mlo = mlo; cx.nr1 = mhi - mlo; cx.nrows = rend - j0; cx.ng = ng;
         cx.pitch = gdp->pitch;
-        cx.col_ok = i0 + tid < nx;
-        cx.cs.init(i0 + tid, nx);
+        cx.col_ok = i0 + cx.lt < nx;
+        cx.cs.init(i0 + cx.lt, nx);
         cx.beta = (kind == K1_ITER) ? (T)st->beta : (T)0;
         cx.pend = (kind == K1_ITER) ? (T)st->pending : (T)0;
         const int dsel = st->dsel;
@@ -768,7 +782,7 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
       gbase += ng;
       if (aborted && tid == 0) { rc.ctl[CTL_ABORT] = 1; flag_timeout(st); }
       if (kind == K1_SPMV) continue;
-      if (unit_reduce2<TX>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt1, red, &rc.ctl[CTL_FLAG])) {
+      if (unit_reduce2<G::NC>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt1, red, &rc.ctl[CTL_FLAG])) {
         if (tid == 0) {
           if (kind == K1_ITER) {
             const double dq = acc0;
@@ -825,7 +839,10 @@ struct K2Geom {
   // 42 KB of ring.
   static constexpr int LIVE = (LD + 2 + RB - 1) / RB + 1;
   static constexpr int NSG = RB == 1 ? LD + 4 : ring_groups(42000, GROUP, LIVE);
-  static constexpr int NT = TX + 32;
+  // NGRP warp groups of TX compute threads (with 2, each step's work is split:
+  // group 0 t, r' and the waits, group 1 s = Z t and its stores; measured no
+  // faster than 1 on this GPU), then the producer warp
+  static constexpr int NGRP = 1, NC = NGRP * TX, NT = NC + 32;
   static constexpr size_t SMEM = 128 + 256 + (size_t)NSG * GROUP +
                                  sizeof(T) * ((size_t)NRN * WRC + (size_t)NTT * WTC) + 16 * (NT / 32) + 64;
 };
@@ -853,14 +870,14 @@ struct K2Unit {
   const T *zwrap;
   uint64_t timeout_ns;
   uint32_t fslot, fpar, eslot;
-  int tid, nx, ny, mlo, j0, i0, nr1, nrows, pitch, ng, nseen, nrel, col;
+  int tid, lt, grp, nx, ny, mlo, j0, i0, nr1, nrows, pitch, ng, nseen, nrel, col;
   bool col_ok, edge;
   ColStore<T> cs;
   T alpha;
   DotAcc<T> dot0, dot1;
 
   __device__ __forceinline__ void begin(const unsigned char *ring, uint32_t gbase) {
-    ring_lo = ring + tid * ESZ;
+    ring_lo = ring + lt * ESZ;
     ring_hi = ring_lo + (size_t)NSG * G::GROUP;
     fslot = gbase % NSG;
     fpar = (gbase / NSG) & 1u;
@@ -875,7 +892,7 @@ struct K2Unit {
     return reinterpret_cast<const T *>(sb + off) + irow * w;
   }
 
-  // t = D^-1 (Z^T r') on row mt (phase KT = K - 1) at column c = tid + dc of
+  // t = D^-1 (Z^T r') on row mt (phase KT = K - 1) at column c = lt + dc of
   // [i0-R, i0+TX+R): dc = 0 (main) or TX (the right halo columns)
   template <int KT>
   __device__ __forceinline__ T tcol(const unsigned char *bz, int dc, int mt) const {
@@ -888,7 +905,7 @@ struct K2Unit {
       acc = fma(fld(bz, G::OFF_Z + s * FBZ, IZ, G::WZ)[G::HZ - R + dc], rrow[R + P::dx(s)], acc);
     }
     if (edge && mt < ny) {                   // rows >= ny: zero t (Z, D^-1 and r' are zero there)
-      const int cg = i0 - R + tid + dc;
+      const int cg = i0 - R + lt + dc;
       const int cm = cg < 0 ? cg + nx : (cg >= nx ? cg - nx : cg);
 #pragma unroll
       for (int w = 0; w < (NW > 0 ? NW : 1); ++w)
@@ -911,8 +928,9 @@ struct K2Unit {
     // m - 2 - LD (reads t rows of earlier steps), t on row m - 1 (reads r'
     // rows of earlier steps), then r' on row m, the only part that waits for
     // streamed data.
+    const bool ga = G::NGRP == 1 || grp == 0, gb1 = G::NGRP == 1 || grp == 1;
     // s = Z t on row r = m - 2 - LD (rel - 2 - 2 LD = r - j0)
-    if (rel - 2 - 2 * LD >= 0 && rel - 2 - 2 * LD < nrows && col_ok) {
+    if (gb1 && rel - 2 - 2 * LD >= 0 && rel - 2 - 2 * LD < nrows && col_ok) {
       constexpr int KR = K - 2 - LD;
       const T *tr = tt + pmod(KR, G::NTT) * G::WTC;
       T acc = tr[R];
@@ -940,16 +958,16 @@ struct K2Unit {
       dot1.add(rv, rv);
     }
     // t on row mt = m - 1 (rel - 1 - LD = mt - j0)
-    if (rel - 1 - LD >= 0 && rel - 1 <= nr1) {
+    if (ga && rel - 1 - LD >= 0 && rel - 1 <= nr1) {
       const unsigned char *bz = gb[gback(K, 1)];
       const int mt = mlo + rel - 1;
       T *tm = tt + pmod(K - 1, G::NTT) * G::WTC;
       tm[0] = tcol<K - 1>(bz, 0, mt);
-      if (tid < G::WTC - TX) tm[TX] = tcol<K - 1>(bz, TX, mt);
+      if (lt < G::WTC - TX) tm[TX] = tcol<K - 1>(bz, TX, mt);
     }
     bool got = true, waited = false;
     // r' on row m over [i0-2R, i0+TX+2R)
-    if (rel <= nr1) {
+    if (ga && rel <= nr1) {
       if constexpr (I == 0) {
         got = mbar_wait_or_abort(&full[fslot], fpar, timeout_ns, abort);
         waited = true;
@@ -961,13 +979,13 @@ struct K2Unit {
       T v = Rr[k0];
       if (kind == K2_ITER) v = fma(-alpha, Qr[k0], v);
       rnm[0] = v;
-      if (tid < G::WRC - TX) {
+      if (lt < G::WRC - TX) {
         T v2 = Rr[k0 + TX];
         if (kind == K2_ITER) v2 = fma(-alpha, Qr[k0 + TX], v2);
         rnm[TX] = v2;
       }
     }
-    if (!compute_sync_and<TX>(got)) return false;
+    if (!compute_sync_and<G::NC>(got)) return false;
     if (waited) ++nseen;
     // row m - 2 - LD is finished: at the last row of its group, release the group
     if constexpr (pmod(K - 1 - LD, RB) == 0) {
@@ -1025,7 +1043,7 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
     return kind != K2_APPLY && *(const volatile int32_t *)&st->done != 0;
   };
 
-  if (tid >= TX) {
+  if (tid >= G::NC) {
     // ---- producer warp
     auto setup = [&](int ui, int f, FieldCopy &c, bool &has, int &mlo, int &ng) -> bool {
       const Unit un = p.units[ui];
@@ -1056,7 +1074,7 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
     };
     const uint32_t gq =
         produce_all<G::NSG, G::RB>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, setup);
-    if (tid == TX) rc.ctl[CTL_ARMED] = (int)gq;
+    if (tid == G::NC) rc.ctl[CTL_ARMED] = (int)gq;
   } else {
     // ---- compute threads
     uint32_t gbase = 0, seen = 0;
@@ -1075,11 +1093,12 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
       const int rsel = (kind == K2_APPLY) ? 0 : st->rsel;
       if (!aborted) {
         K2Unit<T, TX, P, KIND> cx;
-        cx.tid = tid; cx.rn = rn + tid; cx.tt = tt + tid; cx.full = rc.full; cx.empty = rc.empty;
+        cx.tid = tid; cx.grp = tid / TX; cx.lt = tid - cx.grp * TX;
+        cx.rn = rn + cx.lt; cx.tt = tt + cx.lt; cx.full = rc.full; cx.empty = rc.empty;
         cx.abort = &rc.ctl[CTL_ABORT]; cx.timeout_ns = p.timeout_ns;
         cx.begin(rc.ring, gbase);
         cx.nx = nx; cx.ny = ny; cx.mlo = mlo; cx.j0 = j0; cx.i0 = i0; cx.nr1 = mhi - mlo;
-        cx.nrows = rend - j0; cx.ng = ng; cx.pitch = gdp->pitch; cx.col = i0 + tid;
+        cx.nrows = rend - j0; cx.ng = ng; cx.pitch = gdp->pitch; cx.col = i0 + cx.lt;
         cx.col_ok = cx.col < nx;
         cx.cs.init(cx.col, nx);
         cx.alpha = (kind == K2_ITER) ? (T)st->alpha : (T)0;
@@ -1094,7 +1113,7 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
       gbase += ng;
       if (aborted && tid == 0) { rc.ctl[CTL_ABORT] = 1; flag_timeout(st); }
       if (kind == K2_APPLY) continue;
-      if (unit_reduce2<TX>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt2, red, &rc.ctl[CTL_FLAG])) {
+      if (unit_reduce2<G::NC>(acc0, acc1, gdp->partial, un.u, gdp->n_units, &st->cnt2, red, &rc.ctl[CTL_FLAG])) {
         if (tid == 0) {
           const double rho_new = acc0, rr = acc1;
           st->rr = rr;
