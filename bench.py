@@ -350,12 +350,19 @@ def run_serve(args, wl_name, wl):
     call_ms = []      # client-side time of the right-hand-side update and of the submit call
     sampler = _sample_clocks(int(os.environ.get("LOCAL_RANK", "0")))
     t0 = time.perf_counter()
+    iter_gap, late_sec = [], {}
+    t_prev = None
     for t_arr, k in zip(arrivals, grid_pick):
         now = time.perf_counter() - t0
+        if t_prev is not None:
+            iter_gap.append(now - t_prev)
         if t_arr > now:
             time.sleep(t_arr - now)
         else:
             late.append(now - t_arr)
+            sec = int(t_arr)
+            late_sec[sec] = max(late_sec.get(sec, 0.0), now - t_arr)
+        t_prev = time.perf_counter() - t0
         ta = time.perf_counter()
         cur[k].add_(noise[k][steps_done[k] % 2])
         steps_done[k] += 1
@@ -396,6 +403,11 @@ def run_serve(args, wl_name, wl):
                    "client_update_ms_p99": float(np.percentile([c[0] for c in call_ms], 99)) if call_ms else 0.0,
                    "client_submit_ms_p99": float(np.percentile([c[1] for c in call_ms], 99)) if call_ms else 0.0,
                    "client_submit_ms_max": float(max(c[1] for c in call_ms)) if call_ms else 0.0,
+                   "submit_late_max_ms": float(max(late)) * 1e3 if late else 0.0,
+                   "submit_late_over_10ms": int(sum(1 for v in late if v > 0.01)),
+                   "client_iter_ms_max": float(max(iter_gap)) * 1e3 if iter_gap else 0.0,
+                   "late_by_second_ms": {str(k): round(v * 1e3, 1) for k, v in sorted(late_sec.items())
+                                         if v > 0.01},
                    "requests": len(results), "failed": len(results) - sum(1 for r in results if r[2] == 0),
                    "grids": {f"{c['nx']}x{c['ny']}": n for c, n in pool}, "hbm_budget_gb": 150,
                    "max_slots": 16, "chunk_iters": args.chunk,

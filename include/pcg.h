@@ -268,8 +268,10 @@ typedef struct pcg_server pcg_server;
  * solution of its grid. */
 int solver_server_create(const pcg_server_opts *opts, pcg_server **out);
 
-/* Register a grid; the handle stays owned by the caller and must outlive the
- * server. Fails with PCG_EBUDGET if the grid's resident bytes do not fit. */
+/* Register a grid; the handle stays owned by the caller, must outlive the
+ * server, and must not be used outside it while the server runs. In a mixed
+ * precision server the grid's binary32 planes are built here and counted.
+ * Fails with PCG_EBUDGET if the grid's resident bytes do not fit. */
 int solver_server_register(pcg_server *s, pcg_handle *h, int32_t *grid_id);
 
 /* Queue a solve of grid grid_id with right-hand side b ([ny][nx], host or

@@ -488,6 +488,7 @@ static int plan_build_t(LoopPlan &L, pcg_handle *const *hs, int n, bool with_gra
     for (size_t mi = 0; mi < g.size(); ++mi) {
       auto &P = hs[g[mi]]->*planes;
       gds.push_back(P.gd);
+      gds.back().u_off = (int32_t)units.size();       // the member's units are contiguous
       for (Unit u : P.units) { u.g = (int16_t)mi; units.push_back(u); }
     }
     void *gd_dev = nullptr, *un_dev = nullptr;
@@ -864,11 +865,14 @@ static int choose_tx(int nx, int elem_size) {
 }
 
 // Strip height: about 600 units when the grid allows (the persistent CTAs
-// then take one to a few units each), a multiple of 8 rows in 8..64.
-static int choose_ty(int nx, int ny, int tx) {
+// then take one to a few units each), a multiple of 8 rows in min_ty..64.
+// A unit costs its height plus the pipeline depth in steps (2 + 2 LD for the
+// preconditioner kernel), which weighs more in the binary32 kernels: their
+// strips are at least 16 rows tall.
+static int choose_ty(int nx, int ny, int tx, int min_ty) {
   const int ntx = (nx + tx - 1) / tx;
   const int ty = (int)((double)ntx * ny / 600.0) / 8 * 8;
-  return std::max(8, std::min(64, ty));
+  return std::max(min_ty, std::min(64, ty));
 }
 
 }  // namespace pcg
@@ -960,9 +964,9 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     if (opts->tile_x != 0 && opts->tile_x != 64 && opts->tile_x != 128) { set_error("tile_x must be 64 or 128"); return PCG_EINVAL; }
     if (opts->tile_y != 0 && (opts->tile_y < 4 || opts->tile_y > 256)) { set_error("tile_y must be 4..256"); return PCG_EINVAL; }
     h->tx = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 8);
-    h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx);
+    h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx, 8);
     h->tx32 = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 4);
-    h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32);
+    h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32, 16);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     rc = upload_planes(h.get(), h->p64, s);
     if (rc) { h->p64.release(); return rc; }

@@ -82,7 +82,9 @@ enum {
 template <typename T>
 struct GridDev {
   int32_t nx, ny, pitch, ty;
-  int32_t n_units, n_wrap, pad0, pad1;
+  int32_t n_units, n_wrap;
+  int32_t u_off;           // index of this grid's first unit in the launch's unit list
+  int32_t pad1;
   const T *ce, *cn, *a, *dinv;
   const T *z[8];
   const T *zwrap;          // [ny][n_wrap]

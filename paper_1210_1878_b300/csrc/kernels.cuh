@@ -338,10 +338,19 @@ __device__ __forceinline__ void compute_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory");
 }
 
+// A CTA's next unit after unit ui when ui's whole grid is to be skipped
+// (done): the first index at or past u_end = u_off + n_units of that grid in
+// the CTA's stride. Units of a grid are contiguous in a launch's list.
+__device__ __forceinline__ int skip_grid(int ui, int u_end) {
+  const int g = (int)gridDim.x;
+  return u_end <= ui ? ui + g : ui + (u_end - ui + g - 1) / g * g;
+}
+
 // The producer warp's loop: lane f issues the copies of field f of every
-// group of the CTA's units, in order. setup(ui, f, c, has, mlo, ng) describes
-// unit ui's field f (returns false for a unit to skip). Returns the number of
-// groups armed; stops early once the CTA is aborting.
+// group of the CTA's units, in order. setup(ui, f, c, has, mlo, ng, u_end)
+// describes unit ui's field f (returns false when ui's grid is to be skipped,
+// with u_end the end of that grid's units). Returns the number of groups
+// armed; stops early once the CTA is aborting.
 template <int NSG, int RB, class Setup>
 __device__ __forceinline__ uint32_t produce_all(const KParams &p, unsigned char *ring, int group_bytes, uint64_t *full,
                                                 uint64_t *empty, volatile int *ctl, Setup setup) {
@@ -351,8 +360,11 @@ __device__ __forceinline__ uint32_t produce_all(const KParams &p, unsigned char 
   for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
     FieldCopy c{};
     bool has = false;
-    int mlo = 0, ng = 0;
-    if (!setup(ui, lane, c, has, mlo, ng)) continue;
+    int mlo = 0, ng = 0, u_end = 0;
+    if (!setup(ui, lane, c, has, mlo, ng, u_end)) {
+      ui = skip_grid(ui, u_end) - (int)gridDim.x;
+      continue;
+    }
     const int g_un = p.units[ui].g;
     const bool skip_first = (p.dbg_skip_unit == ui) && lane == 0;
     if constexpr (RB > 1)
@@ -575,7 +587,9 @@ struct K1Unit {
     return reinterpret_cast<const T *>(sb + F) + irow * w;
   }
 
-  template <int K>
+  // CHK = false: a step of the unit's steady part, where every phase is
+  // active (the range checks are skipped).
+  template <int K, bool CHK>
   __device__ __forceinline__ bool step(int rel) {
     constexpr int I = K % RB;
     if constexpr (I == 0) {
@@ -589,7 +603,7 @@ struct K1Unit {
     // Loads of a step come before its shared-memory stores: q on row m - 2
     // first (it reads d' rows written in earlier steps), then d' on row m.
     // q = A d' on row r = m - 2 (rel - 3 = r - j0)
-    const bool qrow = rel >= 3 && rel - 3 < nrows && col_ok;
+    const bool qrow = (!CHK || (rel >= 3 && rel - 3 < nrows)) && col_ok;
     if (gb1 && qrow) {
       const unsigned char *br = gb[gback(K, 2)], *bs = gb[gback(K, 3)];
       constexpr int IR = pmod(K - 2, RB), IS = pmod(K - 3, RB);
@@ -632,7 +646,7 @@ struct K1Unit {
     }
     // last: d' on row m (the only part that waits for streamed data)
     bool got = true, waited = false;
-    if (ga && rel <= nr1) {                            // row m = mlo + rel is streamed
+    if (ga && (!CHK || rel <= nr1)) {                  // row m = mlo + rel is streamed
       if constexpr (I == 0) {
         got = mbar_wait_or_abort(&full[fslot], fpar, timeout_ns, abort);
         waited = true;
@@ -654,7 +668,7 @@ struct K1Unit {
     if (waited) ++nseen;
     // row m - 3 is finished: at the last row of its group, release the group
     if constexpr (pmod(K - 2, RB) == 0) {
-      if (rel >= 3) {
+      if (!CHK || rel >= 3) {
         if (tid == 0) mbar_arrive(&empty[eslot]);
         if (++eslot == (uint32_t)NSG) eslot = 0;
         ++nrel;
@@ -664,12 +678,21 @@ struct K1Unit {
   }
 
   // All steps of the unit (rel = 0 .. nrows + 2); releases the unit's groups.
+  // Blocks of 8 steps inside [3, nr1] (both phases active) skip the checks.
   __device__ __forceinline__ bool run() {
     const int last = nrows + 2;
     for (int b = 0; b <= last; b += 8) {
+      if (b >= 3 && b + 7 <= nr1) {
+#define PCG_K1_STEADY(K) \
+  if (!step<K, false>(b + K)) return false;
+        PCG_K1_STEADY(0) PCG_K1_STEADY(1) PCG_K1_STEADY(2) PCG_K1_STEADY(3)
+        PCG_K1_STEADY(4) PCG_K1_STEADY(5) PCG_K1_STEADY(6) PCG_K1_STEADY(7)
+#undef PCG_K1_STEADY
+        continue;
+      }
 #define PCG_K1_STEP(K) \
   if (b + K > last) break; \
-  if (!step<K>(b + K)) return false;
+  if (!step<K, true>(b + K)) return false;
       PCG_K1_STEP(0) PCG_K1_STEP(1) PCG_K1_STEP(2) PCG_K1_STEP(3)
       PCG_K1_STEP(4) PCG_K1_STEP(5) PCG_K1_STEP(6) PCG_K1_STEP(7)
 #undef PCG_K1_STEP
@@ -709,9 +732,10 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
 
   if (tid >= G::NC) {
     // ---- producer warp
-    auto setup = [&](int ui, int f, FieldCopy &c, bool &has, int &mlo, int &ng) -> bool {
+    auto setup = [&](int ui, int f, FieldCopy &c, bool &has, int &mlo, int &ng, int &u_end) -> bool {
       const Unit un = p.units[ui];
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
+      u_end = gdp->u_off + gdp->n_units;
       if (skip_unit(gdp->st)) return false;
       const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
       const int mhi = min(j0 + gdp->ty, gdp->ny);
@@ -753,7 +777,10 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
       const Unit un = p.units[ui];
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
       SolveState *st = gdp->st;
-      if (skip_unit(st)) continue;
+      if (skip_unit(st)) {
+        ui = skip_grid(ui, gdp->u_off + gdp->n_units) - (int)gridDim.x;
+        continue;
+      }
       const int nx = gdp->nx, ny = gdp->ny;
       const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
       const int rend = min(j0 + gdp->ty, ny);
@@ -914,7 +941,9 @@ struct K2Unit {
     return acc * fld(bz, G::OFF_DI, IZ, G::WZ)[G::HZ - R + dc];
   }
 
-  template <int K>
+  // CHK = false: a step of the unit's steady part, where every phase is
+  // active (the range checks are skipped).
+  template <int K, bool CHK>
   __device__ __forceinline__ bool step(int rel) {
     constexpr int I = K % RB;
     if constexpr (I == 0) {
@@ -930,7 +959,7 @@ struct K2Unit {
     // streamed data.
     const bool ga = G::NGRP == 1 || grp == 0, gb1 = G::NGRP == 1 || grp == 1;
     // s = Z t on row r = m - 2 - LD (rel - 2 - 2 LD = r - j0)
-    if (gb1 && rel - 2 - 2 * LD >= 0 && rel - 2 - 2 * LD < nrows && col_ok) {
+    if (gb1 && (!CHK || (rel - 2 - 2 * LD >= 0 && rel - 2 - 2 * LD < nrows)) && col_ok) {
       constexpr int KR = K - 2 - LD;
       const T *tr = tt + pmod(KR, G::NTT) * G::WTC;
       T acc = tr[R];
@@ -958,7 +987,7 @@ struct K2Unit {
       dot1.add(rv, rv);
     }
     // t on row mt = m - 1 (rel - 1 - LD = mt - j0)
-    if (ga && rel - 1 - LD >= 0 && rel - 1 <= nr1) {
+    if (ga && (!CHK || (rel - 1 - LD >= 0 && rel - 1 <= nr1))) {
       const unsigned char *bz = gb[gback(K, 1)];
       const int mt = mlo + rel - 1;
       T *tm = tt + pmod(K - 1, G::NTT) * G::WTC;
@@ -967,7 +996,7 @@ struct K2Unit {
     }
     bool got = true, waited = false;
     // r' on row m over [i0-2R, i0+TX+2R)
-    if (ga && rel <= nr1) {
+    if (ga && (!CHK || rel <= nr1)) {
       if constexpr (I == 0) {
         got = mbar_wait_or_abort(&full[fslot], fpar, timeout_ns, abort);
         waited = true;
@@ -989,7 +1018,7 @@ struct K2Unit {
     if (waited) ++nseen;
     // row m - 2 - LD is finished: at the last row of its group, release the group
     if constexpr (pmod(K - 1 - LD, RB) == 0) {
-      if (rel - 2 - LD >= 0) {
+      if (!CHK || rel - 2 - LD >= 0) {
         if (tid == 0) mbar_arrive(&empty[eslot]);
         if (++eslot == (uint32_t)NSG) eslot = 0;
         ++nrel;
@@ -999,12 +1028,21 @@ struct K2Unit {
   }
 
   // All steps of the unit (rel = 0 .. nrows + 2 LD + 1); releases the unit's groups.
+  // Blocks of 8 steps inside [2 + 2 LD, nr1] (all phases active) skip the checks.
   __device__ __forceinline__ bool run() {
     const int last = nrows + 2 * LD + 1;
     for (int b = 0; b <= last; b += 8) {
+      if (b >= 2 + 2 * LD && b + 7 <= nr1) {
+#define PCG_K2_STEADY(K) \
+  if (!step<K, false>(b + K)) return false;
+        PCG_K2_STEADY(0) PCG_K2_STEADY(1) PCG_K2_STEADY(2) PCG_K2_STEADY(3)
+        PCG_K2_STEADY(4) PCG_K2_STEADY(5) PCG_K2_STEADY(6) PCG_K2_STEADY(7)
+#undef PCG_K2_STEADY
+        continue;
+      }
 #define PCG_K2_STEP(K) \
   if (b + K > last) break; \
-  if (!step<K>(b + K)) return false;
+  if (!step<K, true>(b + K)) return false;
       PCG_K2_STEP(0) PCG_K2_STEP(1) PCG_K2_STEP(2) PCG_K2_STEP(3)
       PCG_K2_STEP(4) PCG_K2_STEP(5) PCG_K2_STEP(6) PCG_K2_STEP(7)
 #undef PCG_K2_STEP
@@ -1045,9 +1083,10 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
 
   if (tid >= G::NC) {
     // ---- producer warp
-    auto setup = [&](int ui, int f, FieldCopy &c, bool &has, int &mlo, int &ng) -> bool {
+    auto setup = [&](int ui, int f, FieldCopy &c, bool &has, int &mlo, int &ng, int &u_end) -> bool {
       const Unit un = p.units[ui];
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
+      u_end = gdp->u_off + gdp->n_units;
       if (skip_unit(gdp->st)) return false;
       const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
       const int rend = min(j0 + gdp->ty, gdp->ny);
@@ -1083,7 +1122,10 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
       const Unit un = p.units[ui];
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
       SolveState *st = gdp->st;
-      if (skip_unit(st)) continue;
+      if (skip_unit(st)) {
+        ui = skip_grid(ui, gdp->u_off + gdp->n_units) - (int)gridDim.x;
+        continue;
+      }
       const int nx = gdp->nx, ny = gdp->ny;
       const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
       const int rend = min(j0 + gdp->ty, ny);

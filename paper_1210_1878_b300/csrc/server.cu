@@ -90,6 +90,11 @@ void pcg_server::run() {
   // (binary64 residual; the end, or a binary32 inner solve set up) -> ITER
   // (the inner solve, advanced with the others) -> its last x32 update and the
   // binary64 correction -> START again.
+  //
+  // The chunks run through one batched plan over every registered grid,
+  // built again only when a grid is registered: a grid with no request
+  // iterating has its device state marked done, and the persistent kernels
+  // skip a done grid's units in one step.
   enum { START = 0, ITER = 1 };
   struct Active {
     std::shared_ptr<Request> r;
@@ -99,11 +104,12 @@ void pcg_server::run() {
   };
   std::vector<Active> active;
   std::unique_ptr<LoopPlan> plan;
-  bool plan_dirty = true;
+  size_t plan_grids = 0;
   pcg_opts o;
   fill_opts(&opts.solve, o);
   const bool mixed = o.prec == PCG_MIXED;
   const int chunk = std::max(1, opts.chunk_iters);
+  static const int32_t kOne = 1;
   auto finish = [&](Active &a, int status) {
     a.m.final_status = status;
     if (mixed) mixed_stats(a.m); else member_stats(a.m);
@@ -123,15 +129,22 @@ void pcg_server::run() {
     --in_flight;
     cv_done.notify_all();
   };
-  // the final x of a finished request goes to its output buffer
-  auto retire = [&](Active &a) {
-    int rc = member_store(a.m, stream);
-    if (!rc && cudaStreamSynchronize(stream) != cudaSuccess) rc = PCG_ECUDA;
-    finish(a, rc ? rc : a.m.final_status);
+  // the final x of each finished request goes to its output buffer, one sync for all
+  auto retire_all = [&](std::vector<Active> &done_list) {
+    if (done_list.empty()) return;
+    std::vector<int> rcs(done_list.size(), PCG_OK);
+    for (size_t i = 0; i < done_list.size(); ++i) rcs[i] = member_store(done_list[i].m, stream);
+    const bool ok = cudaStreamSynchronize(stream) == cudaSuccess;
+    for (size_t i = 0; i < done_list.size(); ++i)
+      finish(done_list[i], rcs[i] ? rcs[i] : (ok ? done_list[i].m.final_status : PCG_ECUDA));
+    done_list.clear();
   };
+  auto state_of = [&](Active &a) -> SolveState & { return mixed ? *a.m.h->st32_host : *a.m.st_host; };
+  auto dev_state = [&](Active &a) { return mixed ? a.m.h->p32.st : a.m.h->p64.st; };
 
   for (;;) {
     std::vector<std::shared_ptr<Request>> admitted;
+    std::vector<pcg_handle *> all;
     {
       std::unique_lock<std::mutex> lk(mu);
       cv_work.wait(lk, [&] { return stop || !active.empty() || !queue.empty(); });
@@ -143,6 +156,46 @@ void pcg_server::run() {
         admitted.push_back(r);
         ++in_flight;
         it = queue.erase(it);
+      }
+      if (grids.size() != plan_grids)
+        for (auto &g : grids) all.push_back(g.h);
+    }
+    // the batched plan over every registered grid (new registrations only);
+    // grids without an iterating request are marked done on the device
+    if (!all.empty()) {
+      int rc = PCG_OK;
+      for (pcg_handle *h : all) {
+        if (!rc) rc = plan_single(h);
+        if (!rc && mixed) rc = ensure_f32(h, stream);
+      }
+      for (pcg_handle *h : all) {
+        bool busy = false;
+        for (auto &a : active) busy = busy || a.m.h == h;
+        if (busy || rc) continue;
+        if (cudaMemcpyAsync(&h->p64.st->done, &kOne, sizeof(int32_t), cudaMemcpyHostToDevice, stream) != cudaSuccess ||
+            (mixed && cudaMemcpyAsync(&h->p32.st->done, &kOne, sizeof(int32_t), cudaMemcpyHostToDevice, stream) !=
+                          cudaSuccess))
+          rc = PCG_ECUDA;
+      }
+      if (!rc) {
+        auto np = std::make_unique<LoopPlan>();
+        rc = mixed ? plan_build32(*np, all.data(), (int)all.size(), true, ls_dev, stream)
+                   : plan_build(*np, all.data(), (int)all.size(), true, ls_dev, stream);
+        if (!rc && cudaStreamSynchronize(stream) != cudaSuccess) rc = PCG_ECUDA;
+        if (!rc) { plan = std::move(np); plan_grids = all.size(); }
+      }
+      if (rc) {
+        for (auto &a : active) finish(a, rc);
+        active.clear();
+        for (auto &r : admitted) {
+          Active a;
+          a.r = r;
+          a.m.h = grids[r->grid].h;
+          a.m.stats = &r->stats;
+          a.m.st_host = a.m.h->st_host;
+          finish(a, rc);
+        }
+        continue;
       }
     }
     // admission: inputs on the device (the warm start keeps the grid's last x)
@@ -164,47 +217,56 @@ void pcg_server::run() {
       active.push_back(std::move(a));
     }
     if (active.empty()) continue;
-    // START phase: per-request setup steps
+    // START phase. binary64: the init kernels. Mixed: the binary64 residual
+    // of every starting request, one sync, then each one's decision and, if
+    // it goes on, its binary32 inner solve set up.
     const int budget_cap = o.max_iter;
-    std::vector<Active> next;
-    for (auto &a : active) {
-      if (a.phase != START) { next.push_back(std::move(a)); continue; }
+    std::vector<Active> next, retiring;
+    std::vector<int> start_rc(active.size(), PCG_OK);
+    bool any_start = false;
+    for (size_t i = 0; i < active.size(); ++i) {
+      Active &a = active[i];
+      if (a.phase != START) continue;
       pcg_handle *h = a.m.h;
-      int rc = PCG_OK;
-      if (!mixed) {
-        rc = members_arm(*h->plan64, h->ls_host, 1, 1, stream);
-        if (!rc) rc = single_launch(h, false, 1, K1_RESID_INIT, stream);
-        if (!rc) rc = single_launch(h, false, 2, K2_INIT, stream);
-        if (rc) { finish(a, rc); continue; }
-        a.phase = ITER;
-        plan_dirty = true;
-        next.push_back(std::move(a));
-        continue;
-      }
-      rc = members_arm(*h->plan64, h->ls_host, 1, 1, stream);
+      int rc = members_arm(*h->plan64, h->ls_host, 1, 1, stream);
       if (!rc) rc = single_launch(h, false, 1, K1_RESID_INIT, stream);
-      if (!rc && cudaMemcpyAsync(a.m.st_host, h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream) != cudaSuccess) rc = PCG_ECUDA;
-      if (!rc && cudaStreamSynchronize(stream) != cudaSuccess) rc = PCG_ECUDA;
-      if (rc) { finish(a, rc); continue; }
-      const int budget = budget_cap > 0 ? budget_cap : std::max(h->G.n, 1);
-      int err = PCG_OK;
-      const bool over = mixed_prepare_inner(a.m, o, budget, a.outer, stream, &err);
-      if (err) { finish(a, err); continue; }
-      if (over) { retire(a); continue; }
-      rc = members_arm(*h->plan32, h->ls_host, 1, 1, stream);
-      if (!rc) rc = single_launch(h, true, 1, K1_RESID_INIT, stream);
-      if (!rc) rc = single_launch(h, true, 2, K2_INIT, stream);
-      if (rc) { finish(a, rc); continue; }
-      a.outer += 1;
+      if (!mixed) {
+        if (!rc) rc = single_launch(h, false, 2, K2_INIT, stream);
+      } else if (!rc &&
+                 cudaMemcpyAsync(a.m.st_host, h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream) !=
+                     cudaSuccess) {
+        rc = PCG_ECUDA;
+      }
+      start_rc[i] = rc;
+      any_start = true;
+    }
+    if (mixed && any_start && cudaStreamSynchronize(stream) != cudaSuccess)
+      for (size_t i = 0; i < active.size(); ++i)
+        if (active[i].phase == START && !start_rc[i]) start_rc[i] = PCG_ECUDA;
+    for (size_t i = 0; i < active.size(); ++i) {
+      Active &a = active[i];
+      if (a.phase != START) { next.push_back(std::move(a)); continue; }
+      if (start_rc[i]) { finish(a, start_rc[i]); continue; }
+      pcg_handle *h = a.m.h;
+      if (mixed) {
+        const int budget = budget_cap > 0 ? budget_cap : std::max(h->G.n, 1);
+        int err = PCG_OK;
+        const bool over = mixed_prepare_inner(a.m, o, budget, a.outer, stream, &err);
+        if (err) { finish(a, err); continue; }
+        if (over) { retiring.push_back(std::move(a)); continue; }
+        int rc = members_arm(*h->plan32, h->ls_host, 1, 1, stream);
+        if (!rc) rc = single_launch(h, true, 1, K1_RESID_INIT, stream);
+        if (!rc) rc = single_launch(h, true, 2, K2_INIT, stream);
+        if (rc) { finish(a, rc); continue; }
+        a.outer += 1;
+      }
       a.phase = ITER;
-      plan_dirty = true;
       next.push_back(std::move(a));
     }
     active.swap(next);
+    retire_all(retiring);
     if (active.empty()) continue;
     // states of the iterating requests (some may be done already)
-    auto state_of = [&](Active &a) -> SolveState & { return mixed ? *a.m.h->st32_host : *a.m.st_host; };
-    auto dev_state = [&](Active &a) { return mixed ? a.m.h->p32.st : a.m.h->p64.st; };
     for (auto &a : active) cudaMemcpyAsync(&state_of(a), dev_state(a), sizeof(SolveState), cudaMemcpyDeviceToHost, stream);
     if (cudaStreamSynchronize(stream) != cudaSuccess) {
       for (auto &a : active) finish(a, PCG_ECUDA);
@@ -215,15 +277,6 @@ void pcg_server::run() {
     for (auto &a : active) n_iter += (a.phase == ITER && !state_of(a).done) ? 1 : 0;
     // advance every iterating request together by up to `chunk` iterations
     if (n_iter > 0) {
-      if (plan_dirty) {
-        plan = std::make_unique<LoopPlan>();
-        std::vector<pcg_handle *> hs;
-        for (auto &a : active) hs.push_back(a.m.h);
-        int rc = mixed ? plan_build32(*plan, hs.data(), (int)hs.size(), true, ls_dev, stream)
-                       : plan_build(*plan, hs.data(), (int)hs.size(), true, ls_dev, stream);
-        if (rc) { for (auto &a : active) finish(a, rc); active.clear(); continue; }
-        plan_dirty = false;
-      }
       int rc = members_arm(*plan, ls_host, n_iter, chunk, stream);
       if (!rc) rc = members_loop(*plan, ls_host, chunk, stream);
       for (auto &a : active) cudaMemcpyAsync(&state_of(a), dev_state(a), sizeof(SolveState), cudaMemcpyDeviceToHost, stream);
@@ -233,35 +286,50 @@ void pcg_server::run() {
         continue;
       }
     }
-    // requests whose iteration ended
-    std::vector<Active> still;
+    // requests whose iteration ended. binary64: x update and true residual of
+    // all of them, one sync, then each one's decision.
+    std::vector<Active> still, ended;
     for (auto &a : active) {
       const SolveState &st = state_of(a);
-      if (!st.done && st.status == PCG_OK) { still.push_back(std::move(a)); continue; }
-      pcg_handle *h = a.m.h;
-      plan_dirty = true;
-      int rc;
-      if (mixed) {
-        // last x32 update, then the binary64 correction; back to START
-        rc = single_launch(h, true, 0, 0, stream);
-        if (!rc) rc = mixed_apply_correction(a.m, stream);
-        if (rc) { finish(a, rc); continue; }
-        if (a.m.final_status >= 0) { retire(a); continue; }
-        a.phase = START;
-        still.push_back(std::move(a));
-        continue;
+      if (!st.done && st.status == PCG_OK) still.push_back(std::move(a));
+      else ended.push_back(std::move(a));
+    }
+    if (!ended.empty()) {
+      std::vector<int> rcs(ended.size(), PCG_OK);
+      for (size_t i = 0; i < ended.size(); ++i) {
+        Active &a = ended[i];
+        pcg_handle *h = a.m.h;
+        if (mixed) {
+          // last x32 update, then the binary64 correction
+          rcs[i] = single_launch(h, true, 0, 0, stream);
+          if (!rcs[i]) rcs[i] = mixed_apply_correction(a.m, stream);
+        } else {
+          rcs[i] = members_close(*h->plan64, stream);
+          if (!rcs[i] &&
+              cudaMemcpyAsync(a.m.st_host, h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+            rcs[i] = PCG_ECUDA;
+        }
       }
-      rc = members_close(*h->plan64, stream);
-      if (!rc && cudaMemcpyAsync(a.m.st_host, h->p64.st, sizeof(SolveState), cudaMemcpyDeviceToHost, stream) != cudaSuccess) rc = PCG_ECUDA;
-      if (!rc && cudaStreamSynchronize(stream) != cudaSuccess) rc = PCG_ECUDA;
-      if (rc) { finish(a, rc); continue; }
-      int err = PCG_OK;
-      const bool again = member_decide(a.m, o, false, stream, &err);
-      if (err) { finish(a, err); continue; }
-      if (again) { a.phase = START; still.push_back(std::move(a)); continue; }
-      retire(a);
+      if (!mixed && cudaStreamSynchronize(stream) != cudaSuccess)
+        for (auto &rc : rcs) rc = rc ? rc : PCG_ECUDA;
+      for (size_t i = 0; i < ended.size(); ++i) {
+        Active &a = ended[i];
+        if (rcs[i]) { finish(a, rcs[i]); continue; }
+        if (mixed) {
+          if (a.m.final_status >= 0) { retiring.push_back(std::move(a)); continue; }
+          a.phase = START;
+          still.push_back(std::move(a));
+          continue;
+        }
+        int err = PCG_OK;
+        const bool again = member_decide(a.m, o, false, stream, &err);
+        if (err) { finish(a, err); continue; }
+        if (again) { a.phase = START; still.push_back(std::move(a)); continue; }
+        retiring.push_back(std::move(a));
+      }
     }
     active.swap(still);
+    retire_all(retiring);
   }
   // shutting down: whatever is still active is abandoned
   for (auto &a : active) finish(a, PCG_ECANCELLED);
@@ -290,6 +358,12 @@ int solver_server_register(pcg_server *s, pcg_handle *h, int32_t *grid_id) {
   std::lock_guard<std::mutex> lk(s->mu);
   for (auto &g : s->grids)
     if (g.h == h) { set_error("grid already registered"); return PCG_EINVAL; }
+  if (s->opts.solve.prec == PCG_MIXED) {
+    // the binary32 planes are resident too (and counted)
+    int rc = ensure_f32(h, s->stream);
+    if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = PCG_ECUDA;
+    if (rc) return rc;
+  }
   const size_t need = pcg_resident_bytes(h);
   if (s->hbm_used + need > s->opts.hbm_budget_bytes) {
     set_error("registering this grid would exceed the HBM budget");
