@@ -459,6 +459,25 @@ def _kernel_roofline(pcg, h, b, wl, prec, n_wet, zbar, workload):
     return roof
 
 
+def max_over_ranks(value, device="cuda"):
+    """The maximum of a per-rank float over the process group (the slowest
+    rank's time decides a replicated run); the value itself when not
+    distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicated_rate(units_per_rank, ms_max, world):
+    """Whole-job throughput of N independent replicas: every rank did the
+    same units, the job took the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def _time_solves(pcg, torch, h, b, x, opts, steps, warmup, stream, barrier, world):
     for _ in range(warmup):
         st = pcg.pcg_solve(h, b, x, opts)
@@ -474,12 +493,7 @@ def _time_solves(pcg, torch, h, b, x, opts, steps, warmup, stream, barrier, worl
     torch.cuda.synchronize()
     barrier()
     launches = pcg.pcg_kernel_launches() - l0
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(e0.elapsed_time(e1))
     assert all(s.status == pcg.PCG_OK for s in stats), [s.as_dict() for s in stats if s.status]
     return ms, stats, launches
 
@@ -555,7 +569,7 @@ def main():
     st = stats[-1]
     iters = st.iters
     ms_per_step = ms / args.steps
-    value = world * args.steps / (ms / 1e3)
+    value = replicated_rate(args.steps, ms, world)
     worst_true = max(s.true_relres for s in stats)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
@@ -570,13 +584,8 @@ def main():
         pcg.pcg_solve(h, bh, xh, opts)
     e3.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e2.elapsed_time(e3)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_e2e = float(tt.item())
-    e2e_value = world * args.e2e_steps / (ms_e2e / 1e3)
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3))
+    e2e_value = replicated_rate(args.e2e_steps, ms_e2e, world)
     vec_bytes = grid.nx * grid.ny * 8
 
     roof = _kernel_roofline(pcg, h, b, wl, wl["prec"], n_wet, zbar, args.workload)
@@ -590,7 +599,7 @@ def main():
         steps_m = max(3, args.steps // 2)
         ms_m, stats_m, launches_m = _time_solves(pcg, torch, h, b, x, om, steps_m, args.warmup, stream, barrier,
                                                  world)
-        mixed = {"value": world * steps_m / (ms_m / 1e3), "unit": UNIT, "ms_per_step": ms_m / steps_m,
+        mixed = {"value": replicated_rate(steps_m, ms_m, world), "unit": UNIT, "ms_per_step": ms_m / steps_m,
                  "steps": steps_m, "dtype": "f32+f64", "iters_per_solve": stats_m[-1].iters,
                  "outer_per_solve": stats_m[-1].outer_iters,
                  "worst_true_relres": max(s.true_relres for s in stats_m), "gpu_launches": int(launches_m),

@@ -867,8 +867,9 @@ static int choose_tx(int nx, int elem_size) {
 // Strip height: about 600 units when the grid allows (the persistent CTAs
 // then take one to a few units each), a multiple of 8 rows in min_ty..64.
 // A unit costs its height plus the pipeline depth in steps (2 + 2 LD for the
-// preconditioner kernel), which weighs more in the binary32 kernels: their
-// strips are at least 16 rows tall.
+// preconditioner kernel) and a reduction, which weighs more in the binary32
+// kernels: their strips are 64 rows tall (measured best for single large
+// grids and for batches of small ones).
 static int choose_ty(int nx, int ny, int tx, int min_ty) {
   const int ntx = (nx + tx - 1) / tx;
   const int ty = (int)((double)ntx * ny / 600.0) / 8 * 8;
@@ -966,7 +967,7 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     h->tx = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 8);
     h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx, 8);
     h->tx32 = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 4);
-    h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32, 16);
+    h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32, 64);
     cudaStream_t s = (cudaStream_t)cuda_stream;
     rc = upload_planes(h.get(), h->p64, s);
     if (rc) { h->p64.release(); return rc; }
