@@ -239,6 +239,14 @@ def run_batch(args, wl_name, wl):
     hs = [pcg.ainv_setup_grid(g, pattern=wl["pattern"], drop_tol=wl["tau"], tile_x=args.tile_x, tile_y=args.tile_y)
           for g in grids]
     setup_s = time.perf_counter() - t
+    # strip shapes chosen by measurement: one tuning per distinct grid shape
+    # (for the precision of the inner iterations), applied to every member
+    t = time.perf_counter()
+    tiles = {}
+    if not args.tile_x and not args.tile_y:
+        for h, g in zip(hs, grids):
+            tiles[f"{g.nx}x{g.ny}"] = pcg.pcg_autotune(h, wl["prec"])
+    tune_s = time.perf_counter() - t
     bs = [torch.from_numpy(g.b).cuda() for g in grids]
     xs = [torch.zeros_like(b) for b in bs]
     opts = pcg.make_opts(rtol=wl["rtol"], max_iter=5000, prec=wl["prec"], inner_rtol=args.inner_rtol)
@@ -292,6 +300,7 @@ def run_batch(args, wl_name, wl):
         "config": {"workload": wl_name, "members": len(hs), "sizes": sizes,
                    "pattern": "tril(A^2)", "drop_tol": wl["tau"], "rtol": wl["rtol"],
                    "worst_true_relres": worst, "setup_s": setup_s,
+                   "tiles_autotuned": {k: list(v) for k, v in tiles.items()}, "autotune_s": tune_s,
                    "sequential_fp64_solves_per_s": len(hs) / (seq_ms / 1e3),
                    "l2": "members total ~%.2f GB of planes" % (sum(h.resident_bytes for h in hs) / 1e9)},
         "e2e": {"value": len(hs) / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": vec_bytes,

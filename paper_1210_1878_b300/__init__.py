@@ -26,7 +26,7 @@ PCG_FP64, PCG_MIXED = 0, 1
 
 EXPORTED = [
     "ainv_setup", "ainv_factor_host", "pcg_solve", "pcg_solve_batched", "pcg_spmv", "pcg_spmv_noalloc", "pcg_precond_apply",
-    "pcg_apply_f32",
+    "pcg_apply_f32", "pcg_autotune", "pcg_tiles",
     "pcg_ainv_export", "pcg_resident_bytes", "pcg_n_wet", "pcg_free", "pcg_status_string",
     "pcg_last_error_message", "pcg_debug_wait_timeout", "pcg_profile_kernels", "pcg_kernel_launches", "solver_server_create", "solver_server_register", "solver_server_submit",
     "solver_server_wait", "solver_server_cancel", "solver_server_stats", "solver_server_destroy",
@@ -91,6 +91,8 @@ def _load():
         "pcg_spmv_noalloc": (C.c_int, [vp, vp, vp, vp]),
         "pcg_precond_apply": (C.c_int, [vp, vp, vp, vp]),
         "pcg_apply_f32": (C.c_int, [vp, i32, vp, vp, vp]),
+        "pcg_autotune": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32), vp]),
+        "pcg_tiles": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
         "pcg_ainv_export": (C.c_int, [vp, C.POINTER(i32), vp, vp, vp]),
         "pcg_resident_bytes": (C.c_size_t, [vp]),
         "pcg_n_wet": (i32, [vp]),
@@ -274,6 +276,24 @@ def pcg_apply_f32(h: Handle, op: int, v, out, stream=None):
     rc = lib.pcg_apply_f32(h.ptr, int(op), _ptr(v), _ptr(out), _stream(stream))
     if rc != PCG_OK:
         raise PCGError(rc, "pcg_apply_f32")
+
+
+def pcg_autotune(h: Handle, prec: int = 1, stream=None):
+    """Time the strip shapes for precision prec on h, apply and remember the
+    fastest; returns (tile_x, tile_y)."""
+    tx, ty = C.c_int32(), C.c_int32()
+    rc = lib.pcg_autotune(h.ptr, int(prec), C.byref(tx), C.byref(ty), _stream(stream))
+    if rc != PCG_OK:
+        raise PCGError(rc, "pcg_autotune")
+    return tx.value, ty.value
+
+
+def pcg_tiles(h: Handle, prec: int = 0):
+    tx, ty = C.c_int32(), C.c_int32()
+    rc = lib.pcg_tiles(h.ptr, int(prec), C.byref(tx), C.byref(ty))
+    if rc != PCG_OK:
+        raise PCGError(rc, "pcg_tiles")
+    return tx.value, ty.value
 
 
 def pcg_ainv_export(h: Handle):

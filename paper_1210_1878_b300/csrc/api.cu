@@ -12,7 +12,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <memory>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -876,6 +878,54 @@ static int choose_ty(int nx, int ny, int tx, int min_ty) {
   return std::max(min_ty, std::min(64, ty));
 }
 
+// ------------------------------------------------------------ strip autotuner
+// Tuned strip shapes, per grid shape, pattern and precision, for the process:
+// a tuned shape is used by every later handle of that shape.
+struct TuneKey {
+  int nx, ny, pattern, q, prec;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(nx, ny, pattern, q, prec) < std::tie(o.nx, o.ny, o.pattern, o.q, o.prec);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tuned;
+
+static bool tuned_shape(int nx, int ny, int pattern, int q, int prec, int *tx, int *ty) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tuned.find(TuneKey{nx, ny, pattern, q, prec});
+  if (it == g_tuned.end()) return false;
+  *tx = it->second.first;
+  *ty = it->second.second;
+  return true;
+}
+
+// Rebuild the device planes of one precision of h with strips tx x ty (the
+// handle's last solution in those planes is lost).
+static int retile(pcg_handle *h, int prec, int tx, int ty, cudaStream_t s) {
+  int rc;
+  if (prec == PCG_MIXED) {
+    if (h->plan32 && h->tx32 == tx && h->ty32 == ty) return PCG_OK;
+    if (h->plan32) h->bytes -= h->p32.bytes;
+    h->plan32.reset();
+    h->p32.release();
+    h->p32 = DevPlanes<float>{};
+    h->tx32 = tx;
+    h->ty32 = ty;
+    return ensure_f32(h, s);
+  }
+  if (h->tx == tx && h->ty == ty) return PCG_OK;
+  CK(cudaStreamSynchronize(s));
+  h->bytes -= h->p64.bytes;
+  h->plan64.reset();
+  h->p64.release();
+  h->p64 = DevPlanes<double>{};
+  h->tx = tx;
+  h->ty = ty;
+  if ((rc = upload_planes(h, h->p64, s))) return rc;
+  h->bytes += h->p64.bytes;
+  return plan_single(h);
+}
+
 }  // namespace pcg
 
 using namespace pcg;
@@ -968,6 +1018,10 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx, 8);
     h->tx32 = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 4);
     h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32, 64);
+    if (!opts->tile_x && !opts->tile_y) {       // shapes tuned earlier in this process win
+      tuned_shape(grid->nx, grid->ny, opts->pattern, opts->band_q, PCG_FP64, &h->tx, &h->ty);
+      tuned_shape(grid->nx, grid->ny, opts->pattern, opts->band_q, PCG_MIXED, &h->tx32, &h->ty32);
+    }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     rc = upload_planes(h.get(), h->p64, s);
     if (rc) { h->p64.release(); return rc; }
@@ -1183,6 +1237,50 @@ int pcg_ainv_export(const pcg_handle *h, int32_t *n_wet_out, double *D, int32_t 
 size_t pcg_resident_bytes(const pcg_handle *h) { return h ? h->bytes : 0; }
 
 int32_t pcg_n_wet(const pcg_handle *h) { return h ? h->G.n : 0; }
+
+int pcg_autotune(pcg_handle *h, int32_t prec, int32_t *tile_x, int32_t *tile_y, void *cuda_stream) {
+  if (!h || (prec != PCG_FP64 && prec != PCG_MIXED)) { set_error("invalid arguments"); return PCG_EINVAL; }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int rc, tx = 0, ty = 0;
+  const int nx = h->G.nx, ny = h->G.ny;
+  if (!tuned_shape(nx, ny, h->pattern, h->band_q, prec, &tx, &ty)) {
+    // right-hand side: ones (land is zeroed by the packing), in the staging plane
+    {
+      std::vector<double> ones((size_t)nx * ny, 1.0);
+      CK(cudaMemcpyAsync(h->stage, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, s));
+      CK(cudaStreamSynchronize(s));
+    }
+    double best = 1e300;
+    int last_ty = -1;
+    for (int cx : {64, 128}) {
+      last_ty = -1;
+      for (int cy : {8, 16, 32, 64}) {
+        const int eff = std::min(cy, (ny + 7) / 8 * 8);     // a taller strip than the grid is the same shape
+        if (eff == last_ty) continue;
+        last_ty = eff;
+        if ((rc = retile(h, prec, cx, cy, s))) return rc;
+        double m1 = 0, m2 = 0;
+        if ((rc = pcg_profile_kernels(h, h->stage, 3, prec, &m1, &m2, s))) return rc;
+        if ((rc = pcg_profile_kernels(h, h->stage, 10, prec, &m1, &m2, s))) return rc;
+        if (m1 + m2 < best) { best = m1 + m2; tx = cx; ty = cy; }
+      }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[TuneKey{nx, ny, h->pattern, h->band_q, prec}] = {tx, ty};
+  }
+  if ((rc = retile(h, prec, tx, ty, s))) return rc;
+  CK(cudaStreamSynchronize(s));
+  if (tile_x) *tile_x = tx;
+  if (tile_y) *tile_y = ty;
+  return PCG_OK;
+}
+
+int pcg_tiles(pcg_handle *h, int32_t prec, int32_t *tile_x, int32_t *tile_y) {
+  if (!h || !tile_x || !tile_y || (prec != PCG_FP64 && prec != PCG_MIXED)) { set_error("invalid arguments"); return PCG_EINVAL; }
+  *tile_x = prec == PCG_MIXED ? h->tx32 : h->tx;
+  *tile_y = prec == PCG_MIXED ? h->ty32 : h->ty;
+  return PCG_OK;
+}
 
 void pcg_free(pcg_handle *h) {
   if (!h) return;

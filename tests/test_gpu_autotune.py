@@ -1,0 +1,48 @@
+"""Strip-shape autotuner (batching row: tile shapes chosen by measurement):
+the tuned shape is one of the candidates, is applied to the handle, is
+remembered for later handles of the same grid shape, and solves on retiled
+planes still meet the acceptance test (true relative residual <= 1e-10,
+recomputed by the oracle)."""
+import numpy as np
+import pytest
+
+import gridgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# a grid shape used by no other test (the tuned shapes are kept per process)
+CFG = dict(nx=150, ny=97, land=0.3)
+
+
+def _check_solve(pcg, h, g, prec):
+    P = oracle.OracleProblem.from_grid(g)
+    b = P.to_wet(g.b)
+    x = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
+    st = pcg.pcg_solve(h, torch.from_numpy(g.b).cuda(), x, pcg.make_opts(rtol=1e-10, prec=prec))
+    assert st.status == pcg.PCG_OK
+    xw = P.to_wet(x.cpu().numpy())
+    assert np.linalg.norm(b - P.spmv(xw)) / np.linalg.norm(b) <= 1e-10 * (1 + 1e-3)
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_autotune_applies_and_remembers(prec):
+    import paper_1210_1878_b300 as pcg
+    g = gridgen.make_grid(seed=gridgen.seed_for(5), **CFG)
+    h = pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A2, drop_tol=0.05)
+    tx, ty = pcg.pcg_autotune(h, prec)
+    assert tx in (64, 128) and ty in (8, 16, 32, 64)
+    assert pcg.pcg_tiles(h, prec) == (tx, ty)
+    _check_solve(pcg, h, g, prec)
+    # a later handle of the same grid shape starts with the tuned strips
+    g2 = gridgen.make_grid(seed=gridgen.seed_for(6), **CFG)
+    h2 = pcg.ainv_setup_grid(g2, pattern=pcg.PCG_PAT_TRIL_A2, drop_tol=0.05)
+    if prec == 1:
+        pcg.pcg_apply_f32(h2, 0, torch.zeros((g2.ny, g2.nx), dtype=torch.float64, device="cuda"),
+                          torch.zeros((g2.ny, g2.nx), dtype=torch.float64, device="cuda"))
+    assert pcg.pcg_tiles(h2, prec) == (tx, ty)
+    _check_solve(pcg, h2, g2, prec)
+    # a second call is a cache hit: same answer
+    assert pcg.pcg_autotune(h2, prec) == (tx, ty)
