@@ -245,7 +245,7 @@ def run_batch(args, wl_name, wl):
     tiles = {}
     if not args.tile_x and not args.tile_y:
         for h, g in zip(hs, grids):
-            tiles[f"{g.nx}x{g.ny}"] = pcg.pcg_autotune(h, wl["prec"])
+            tiles[f"{g.nx}x{g.ny}"] = pcg.pcg_autotune(h, wl["prec"], objective=1)
     tune_s = time.perf_counter() - t
     bs = [torch.from_numpy(g.b).cuda() for g in grids]
     xs = [torch.zeros_like(b) for b in bs]

@@ -217,13 +217,18 @@ int pcg_apply_f32(pcg_handle *h, int32_t op, const double *v, double *out, void 
  * precision prec (PCG_FP64: the binary64 planes; PCG_MIXED: the binary32
  * planes of the inner iterations) times the two loop kernels of h on strips
  * of 64 or 128 columns by 8, 16, 32 or 64 rows (ten iterations each, on a
- * right-hand side of ones), rebuilds h's planes with the fastest shape and
- * returns it in tile_x, tile_y (either may be NULL). The result is kept for
- * the process, keyed by (nx, ny, pattern, band_q, prec): a later call for the
- * same key applies it without timing, and ainv_setup without explicit tiles
- * uses it. Overwrites the handle's last solution. Not thread-safe for h.
+ * right-hand side of ones), rebuilds h's planes with the best shape and
+ * returns it in tile_x, tile_y (either may be NULL). objective 0: the
+ * shortest kernel time of the grid alone (a single solve); objective 1: the
+ * smallest share of the GPU, kernel time x min(units, resident CTAs) /
+ * resident CTAs (the grid as one member of a batch or of a server's mix).
+ * The result is kept for the process, keyed by (nx, ny, pattern, band_q,
+ * prec, objective): a later call for the same key applies it without timing,
+ * and ainv_setup without explicit tiles uses the objective-0 shapes.
+ * Overwrites the handle's last solution. Not thread-safe for h.
  * Returns PCG_OK, PCG_EINVAL, PCG_ENOMEM or PCG_ECUDA. */
-int pcg_autotune(pcg_handle *h, int32_t prec, int32_t *tile_x, int32_t *tile_y, void *cuda_stream);
+int pcg_autotune(pcg_handle *h, int32_t prec, int32_t objective, int32_t *tile_x, int32_t *tile_y,
+                 void *cuda_stream);
 
 /* The strip shape (columns, rows) of h's planes of precision prec. */
 int pcg_tiles(pcg_handle *h, int32_t prec, int32_t *tile_x, int32_t *tile_y);

@@ -91,7 +91,7 @@ def _load():
         "pcg_spmv_noalloc": (C.c_int, [vp, vp, vp, vp]),
         "pcg_precond_apply": (C.c_int, [vp, vp, vp, vp]),
         "pcg_apply_f32": (C.c_int, [vp, i32, vp, vp, vp]),
-        "pcg_autotune": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32), vp]),
+        "pcg_autotune": (C.c_int, [vp, i32, i32, C.POINTER(i32), C.POINTER(i32), vp]),
         "pcg_tiles": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
         "pcg_ainv_export": (C.c_int, [vp, C.POINTER(i32), vp, vp, vp]),
         "pcg_resident_bytes": (C.c_size_t, [vp]),
@@ -278,11 +278,11 @@ def pcg_apply_f32(h: Handle, op: int, v, out, stream=None):
         raise PCGError(rc, "pcg_apply_f32")
 
 
-def pcg_autotune(h: Handle, prec: int = 1, stream=None):
+def pcg_autotune(h: Handle, prec: int = 1, objective: int = 0, stream=None):
     """Time the strip shapes for precision prec on h, apply and remember the
-    fastest; returns (tile_x, tile_y)."""
+    best (objective 0: alone, 1: as a batch member); returns (tile_x, tile_y)."""
     tx, ty = C.c_int32(), C.c_int32()
-    rc = lib.pcg_autotune(h.ptr, int(prec), C.byref(tx), C.byref(ty), _stream(stream))
+    rc = lib.pcg_autotune(h.ptr, int(prec), int(objective), C.byref(tx), C.byref(ty), _stream(stream))
     if rc != PCG_OK:
         raise PCGError(rc, "pcg_autotune")
     return tx.value, ty.value

@@ -882,17 +882,17 @@ static int choose_ty(int nx, int ny, int tx, int min_ty) {
 // Tuned strip shapes, per grid shape, pattern and precision, for the process:
 // a tuned shape is used by every later handle of that shape.
 struct TuneKey {
-  int nx, ny, pattern, q, prec;
+  int nx, ny, pattern, q, prec, objective;
   bool operator<(const TuneKey &o) const {
-    return std::tie(nx, ny, pattern, q, prec) < std::tie(o.nx, o.ny, o.pattern, o.q, o.prec);
+    return std::tie(nx, ny, pattern, q, prec, objective) < std::tie(o.nx, o.ny, o.pattern, o.q, o.prec, o.objective);
   }
 };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, std::pair<int, int>> g_tuned;
 
-static bool tuned_shape(int nx, int ny, int pattern, int q, int prec, int *tx, int *ty) {
+static bool tuned_shape(int nx, int ny, int pattern, int q, int prec, int objective, int *tx, int *ty) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  auto it = g_tuned.find(TuneKey{nx, ny, pattern, q, prec});
+  auto it = g_tuned.find(TuneKey{nx, ny, pattern, q, prec, objective});
   if (it == g_tuned.end()) return false;
   *tx = it->second.first;
   *ty = it->second.second;
@@ -1018,9 +1018,9 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx, 8);
     h->tx32 = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 4);
     h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32, 64);
-    if (!opts->tile_x && !opts->tile_y) {       // shapes tuned earlier in this process win
-      tuned_shape(grid->nx, grid->ny, opts->pattern, opts->band_q, PCG_FP64, &h->tx, &h->ty);
-      tuned_shape(grid->nx, grid->ny, opts->pattern, opts->band_q, PCG_MIXED, &h->tx32, &h->ty32);
+    if (!opts->tile_x && !opts->tile_y) {       // shapes tuned earlier in this process win (latency objective)
+      tuned_shape(grid->nx, grid->ny, opts->pattern, opts->band_q, PCG_FP64, 0, &h->tx, &h->ty);
+      tuned_shape(grid->nx, grid->ny, opts->pattern, opts->band_q, PCG_MIXED, 0, &h->tx32, &h->ty32);
     }
     cudaStream_t s = (cudaStream_t)cuda_stream;
     rc = upload_planes(h.get(), h->p64, s);
@@ -1238,12 +1238,16 @@ size_t pcg_resident_bytes(const pcg_handle *h) { return h ? h->bytes : 0; }
 
 int32_t pcg_n_wet(const pcg_handle *h) { return h ? h->G.n : 0; }
 
-int pcg_autotune(pcg_handle *h, int32_t prec, int32_t *tile_x, int32_t *tile_y, void *cuda_stream) {
-  if (!h || (prec != PCG_FP64 && prec != PCG_MIXED)) { set_error("invalid arguments"); return PCG_EINVAL; }
+int pcg_autotune(pcg_handle *h, int32_t prec, int32_t objective, int32_t *tile_x, int32_t *tile_y,
+                 void *cuda_stream) {
+  if (!h || (prec != PCG_FP64 && prec != PCG_MIXED) || (objective != 0 && objective != 1)) {
+    set_error("invalid arguments");
+    return PCG_EINVAL;
+  }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int rc, tx = 0, ty = 0;
   const int nx = h->G.nx, ny = h->G.ny;
-  if (!tuned_shape(nx, ny, h->pattern, h->band_q, prec, &tx, &ty)) {
+  if (!tuned_shape(nx, ny, h->pattern, h->band_q, prec, objective, &tx, &ty)) {
     // right-hand side: ones (land is zeroed by the packing), in the staging plane
     {
       std::vector<double> ones((size_t)nx * ny, 1.0);
@@ -1262,11 +1266,19 @@ int pcg_autotune(pcg_handle *h, int32_t prec, int32_t *tile_x, int32_t *tile_y, 
         double m1 = 0, m2 = 0;
         if ((rc = pcg_profile_kernels(h, h->stage, 3, prec, &m1, &m2, s))) return rc;
         if ((rc = pcg_profile_kernels(h, h->stage, 10, prec, &m1, &m2, s))) return rc;
-        if (m1 + m2 < best) { best = m1 + m2; tx = cx; ty = cy; }
+        double cost = m1 + m2;
+        if (objective == 1) {
+          // share of the GPU: a launch over n units holds min(n, resident) of
+          // the resident CTAs for its duration
+          const KernelSet &ks = prec == PCG_MIXED ? h->p32.ks : h->p64.ks;
+          const int nu = prec == PCG_MIXED ? h->p32.n_units : h->p64.n_units;
+          cost = m1 * std::min(nu, ks.ctas1) / (double)ks.ctas1 + m2 * std::min(nu, ks.ctas2) / (double)ks.ctas2;
+        }
+        if (cost < best) { best = cost; tx = cx; ty = cy; }
       }
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tuned[TuneKey{nx, ny, h->pattern, h->band_q, prec}] = {tx, ty};
+    g_tuned[TuneKey{nx, ny, h->pattern, h->band_q, prec, objective}] = {tx, ty};
   }
   if ((rc = retile(h, prec, tx, ty, s))) return rc;
   CK(cudaStreamSynchronize(s));

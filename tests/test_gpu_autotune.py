@@ -29,6 +29,7 @@ def _check_solve(pcg, h, g, prec):
 
 @pytest.mark.parametrize("prec", [1, 0])
 def test_autotune_applies_and_remembers(prec):
+    """Objective 0 (alone): later handles of the shape start with it."""
     import paper_1210_1878_b300 as pcg
     g = gridgen.make_grid(seed=gridgen.seed_for(5), **CFG)
     h = pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A2, drop_tol=0.05)
@@ -46,3 +47,19 @@ def test_autotune_applies_and_remembers(prec):
     _check_solve(pcg, h2, g2, prec)
     # a second call is a cache hit: same answer
     assert pcg.pcg_autotune(h2, prec) == (tx, ty)
+
+
+def test_autotune_throughput_objective():
+    """Objective 1 (as a batch member) is kept apart from objective 0 and
+    applied on request; the retiled handle still solves correctly."""
+    import paper_1210_1878_b300 as pcg
+    cfg = dict(nx=170, ny=61, land=0.3)
+    g = gridgen.make_grid(seed=gridgen.seed_for(7), **cfg)
+    h = pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A2, drop_tol=0.05)
+    tx, ty = pcg.pcg_autotune(h, 1, objective=1)
+    assert tx in (64, 128) and ty in (8, 16, 32, 64)
+    assert pcg.pcg_tiles(h, 1) == (tx, ty)
+    _check_solve(pcg, h, g, 1)
+    with pytest.raises(pcg.PCGError) as e:
+        pcg.pcg_autotune(h, 1, objective=2)
+    assert e.value.status == pcg.PCG_EINVAL
