@@ -330,6 +330,8 @@ def run_serve(args, wl_name, wl):
             grids.append(gridgen.make_grid(seed=gridgen.seed_for(wl["ci"], 10 * si + m), **cfg))
             size_of.append(si)
     hs = [pcg.ainv_setup_grid(g, pattern=wl["pattern"], drop_tol=wl["tau"]) for g in grids]
+    # strip shapes for the grids as members of the server's mix (throughput objective)
+    tiles = {f"{g.nx}x{g.ny}": pcg.pcg_autotune(h, wl["prec"], objective=1) for h, g in zip(hs, grids)}
     opts = pcg.make_opts(rtol=wl["rtol"], max_iter=5000, prec=wl["prec"], inner_rtol=args.inner_rtol)
     srv = pcg.Server(hbm_budget_bytes=150 << 30, max_slots=16, chunk_iters=args.chunk, opts=opts)
     gids = [srv.register(h) for h in hs]
@@ -419,7 +421,7 @@ def run_serve(args, wl_name, wl):
                                          if v > 0.01},
                    "requests": len(results), "failed": len(results) - sum(1 for r in results if r[2] == 0),
                    "grids": {f"{c['nx']}x{c['ny']}": n for c, n in pool}, "hbm_budget_gb": 150,
-                   "max_slots": 16, "chunk_iters": args.chunk,
+                   "max_slots": 16, "chunk_iters": args.chunk, "tiles_autotuned": {k: list(v) for k, v in tiles.items()},
                    "worst_true_relres": max((r[4] for r in ok), default=None)},
         "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99), "mean": float(lat.mean()) if len(lat) else None,
                        "per_size": per_size},
