@@ -77,10 +77,27 @@ static KernelSet pick_tx(int pattern, int q) {
   return KernelSet{};
 }
 
+// Strips whose preconditioner t phase (TX + 2R columns) fills whole warps:
+// 64 - 2R columns for binary64, 124 for binary32 (a multiple of 4, for the
+// 16-byte alignment of the tensor tiles), for tril(A) and tril(A^2).
+static int exact_width(int elem_size, int pattern) {
+  if (pattern != PCG_PAT_TRIL_A && pattern != PCG_PAT_TRIL_A2) return 0;
+  if (elem_size == 8) return pattern == PCG_PAT_TRIL_A2 ? 60 : 62;
+  return 124;
+}
+
 template <typename T>
 static KernelSet pick(int tx, int pattern, int q) {
   if (tx == 64) return pick_tx<T, 64>(pattern, q);
   if (tx == 128) return pick_tx<T, 128>(pattern, q);
+  if (tx != exact_width((int)sizeof(T), pattern)) return KernelSet{};
+  if constexpr (sizeof(T) == 8) {
+    if (tx == 60) return make_set<T, 60, Pat<PCG_PAT_TRIL_A2, 0>>();
+    if (tx == 62) return make_set<T, 62, Pat<PCG_PAT_TRIL_A, 0>>();
+  } else {
+    if (pattern == PCG_PAT_TRIL_A2) return make_set<T, 124, Pat<PCG_PAT_TRIL_A2, 0>>();
+    return make_set<T, 124, Pat<PCG_PAT_TRIL_A, 0>>();
+  }
   return KernelSet{};
 }
 
@@ -719,7 +736,7 @@ bool mixed_prepare_inner(Member &m, const pcg_opts &o, int budget, int outer, cu
     const Unit *un = m.h->p64.units_dev;
     double sc = m.scale;
     void *args[] = {(void *)&g64, (void *)&g32, (void *)&un, &sc};
-    const void *f = m.h->tx == 128 ? (const void *)k_residual_to_f32<128> : (const void *)k_residual_to_f32<64>;
+    const void *f = (const void *)k_residual_to_f32;
     if (m.h->p64.n_units > 0) {
       g_launches.fetch_add(1, std::memory_order_relaxed);
       if (cudaLaunchKernel(f, dim3(m.h->p64.n_units), dim3(m.h->tx), args, 0, s) != cudaSuccess) *err = PCG_ECUDA;
@@ -755,7 +772,7 @@ int mixed_apply_correction(Member &m, cudaStream_t s) {
   const Unit *un = m.h->p64.units_dev;
   double inv = 1.0 / m.scale;
   void *args[] = {(void *)&g64, (void *)&g32, (void *)&un, &inv};
-  const void *f = m.h->tx == 128 ? (const void *)k_correct_f64<128> : (const void *)k_correct_f64<64>;
+  const void *f = (const void *)k_correct_f64;
   if (m.h->p64.n_units > 0) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     CK(cudaLaunchKernel(f, dim3(m.h->p64.n_units), dim3(m.h->tx), args, 0, s));
@@ -857,13 +874,17 @@ std::string status_name(int s) {
   }
 }
 
-// Strip width. binary64 kernels are bound by the FP64 pipe: narrow strips,
-// more CTAs per SM. binary32 kernels: the width that wastes the fewest
-// columns, ties to the wider strip (fewer halo columns per point).
-static int choose_tx(int nx, int elem_size) {
-  if (elem_size == 8) return 64;
-  const int w128 = (nx + 127) / 128 * 128, w64 = (nx + 63) / 64 * 64;
-  return (w128 - nx <= (w64 - nx) + 16) ? 128 : 64;
+// Strip width. binary64 kernels are bound by the FP64 pipe: narrow strips
+// (more CTAs per SM) whose t phase fills whole warps where the pattern allows
+// (64 - 2R columns). binary32 kernels: of the wide strip (124 or 128 columns)
+// and 64, the one that wastes the fewest columns, ties to the wider strip
+// (fewer halo columns per point).
+static int choose_tx(int nx, int elem_size, int pattern) {
+  const int ex = exact_width(elem_size, pattern);
+  if (elem_size == 8) return ex ? ex : 64;
+  const int wide = ex ? ex : 128;
+  const int ww = (nx + wide - 1) / wide * wide, w64 = (nx + 63) / 64 * 64;
+  return (ww - nx <= (w64 - nx) + 16) ? wide : 64;
 }
 
 // Strip height: about 600 units when the grid allows (the persistent CTAs
@@ -1012,11 +1033,15 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     h->pattern = opts->pattern;
     h->band_q = opts->band_q;
     h->tau = opts->drop_tol;
-    if (opts->tile_x != 0 && opts->tile_x != 64 && opts->tile_x != 128) { set_error("tile_x must be 64 or 128"); return PCG_EINVAL; }
+    if (opts->tile_x != 0 && opts->tile_x != 64 && opts->tile_x != 128 &&
+        opts->tile_x != exact_width(8, opts->pattern) && opts->tile_x != exact_width(4, opts->pattern)) {
+      set_error("tile_x must be 64, 128 or the whole-warp width of the pattern (60, 62 binary64; 124 binary32)");
+      return PCG_EINVAL;
+    }
     if (opts->tile_y != 0 && (opts->tile_y < 4 || opts->tile_y > 256)) { set_error("tile_y must be 4..256"); return PCG_EINVAL; }
-    h->tx = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 8);
+    h->tx = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 8, opts->pattern);
     h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx, 8);
-    h->tx32 = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 4);
+    h->tx32 = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 4, opts->pattern);
     h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32, 64);
     if (!opts->tile_x && !opts->tile_y) {       // shapes tuned earlier in this process win (latency objective)
       tuned_shape(grid->nx, grid->ny, opts->pattern, opts->band_q, PCG_FP64, 0, &h->tx, &h->ty);
@@ -1179,7 +1204,7 @@ int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, int32_t p
     if ((rc = launch_k(G64.ks, 1, G64.n_units, kparams(*L, G64, K1_RESID_INIT, 0, 0), s))) return rc;
     double sc = 1.0;
     void *args[] = {(void *)&g64, (void *)&g32, (void *)&un, &sc};
-    const void *f = h->tx == 128 ? (const void *)k_residual_to_f32<128> : (const void *)k_residual_to_f32<64>;
+    const void *f = (const void *)k_residual_to_f32;
     if (h->p64.n_units > 0) CK(cudaLaunchKernel(f, dim3(h->p64.n_units), dim3(h->tx), args, 0, s));
     auto &P32 = h->p32;
     CK(cudaMemsetAsync(P32.plane_start(P32.vec(0)), 0, P32.plane_elems * sizeof(float), s));
@@ -1256,7 +1281,9 @@ int pcg_autotune(pcg_handle *h, int32_t prec, int32_t objective, int32_t *tile_x
     }
     double best = 1e300;
     int last_ty = -1;
-    for (int cx : {64, 128}) {
+    const int ex = exact_width(prec == PCG_MIXED ? 4 : 8, h->pattern);
+    for (int cx : {64, 128, ex}) {
+      if (cx == 0) continue;
       last_ty = -1;
       for (int cy : {8, 16, 32, 64}) {
         const int eff = std::min(cy, (ny + 7) / 8 * 8);     // a taller strip than the grid is the same shape

@@ -507,7 +507,11 @@ struct K1Geom {
   // NGRP warp groups of TX compute threads (with 2, each step's work is split:
   // group 0 d', the x update and the waits, group 1 q = A d' and its stores;
   // measured no faster than 1 on this GPU), then the producer warp
-  static constexpr int NGRP = 1, NC = NGRP * TX, NT = NC + 32;
+  // NCG: compute threads of a group, the strip width rounded up to whole
+  // warps (a strip of 64 - 2R columns lets the t phase of the preconditioner
+  // kernel cover its TX + 2R columns with whole warps, no extra pass)
+  static constexpr int NCG = round_up_c(TX, 32);
+  static constexpr int NGRP = 1, NC = NGRP * NCG, NT = NC + 32;
   static constexpr size_t SMEM = 128 + 256 + (size_t)NSG * GROUP + sizeof(T) * (size_t)NDN * WDN + 16 * (NT / 32) + 64;
 };
 
@@ -654,14 +658,16 @@ struct K1Unit {
       }
       const T *S = fld<G::OFF_S>(gb[0], I, G::WS), *D = fld<G::OFF_D>(gb[0], I, G::WS);
       T *dnm = dn + (K & (G::NDN - 1)) * G::WDN;
-      // d' on row m over columns [i0-1, i0+TX+1)
-      T v = S[G::H - 1];
-      if (kind == K1_ITER) v = fma(beta, D[G::H - 1], v);
-      dnm[0] = v;
-      if (lt < G::WDN - TX) {
-        T v2 = S[G::H - 1 + TX];
-        if (kind == K1_ITER) v2 = fma(beta, D[G::H - 1 + TX], v2);
-        dnm[TX] = v2;
+      // d' on row m over columns [i0-1, i0+TX+1) (threads past the row's width idle)
+      if (G::NCG <= G::WDN || lt < G::WDN) {
+        T v = S[G::H - 1];
+        if (kind == K1_ITER) v = fma(beta, D[G::H - 1], v);
+        dnm[0] = v;
+      }
+      if (lt < G::WDN - G::NCG) {                     // columns past the group's threads
+        T v2 = S[G::H - 1 + G::NCG];
+        if (kind == K1_ITER) v2 = fma(beta, D[G::H - 1 + G::NCG], v2);
+        dnm[G::NCG] = v2;
       }
     }
     if (!compute_sync_and<G::NC>(got)) return false;
@@ -789,13 +795,13 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
       double acc0 = 0.0, acc1 = 0.0;
       if (!aborted) {
         K1Unit<T, TX, KIND> cx;
-        cx.tid = tid; cx.grp = tid / TX; cx.lt = tid - cx.grp * TX;
+        cx.tid = tid; cx.grp = tid / G::NCG; cx.lt = tid - cx.grp * G::NCG;
         cx.dn = dn + cx.lt; cx.full = rc.full; cx.empty = rc.empty; cx.abort = &rc.ctl[CTL_ABORT];
         cx.timeout_ns = p.timeout_ns;
         cx.begin(rc.ring, gbase);
         cx.mlo = mlo; cx.nr1 = mhi - mlo; cx.nrows = rend - j0; cx.ng = ng;
         cx.pitch = gdp->pitch;
-        cx.col_ok = i0 + cx.lt < nx;
+        cx.col_ok = cx.lt < TX && i0 + cx.lt < nx;
         cx.cs.init(i0 + cx.lt, nx);
         cx.beta = (kind == K1_ITER) ? (T)st->beta : (T)0;
         cx.pend = (kind == K1_ITER) ? (T)st->pending : (T)0;
@@ -869,7 +875,8 @@ struct K2Geom {
   // NGRP warp groups of TX compute threads (with 2, each step's work is split:
   // group 0 t, r' and the waits, group 1 s = Z t and its stores; measured no
   // faster than 1 on this GPU), then the producer warp
-  static constexpr int NGRP = 1, NC = NGRP * TX, NT = NC + 32;
+  static constexpr int NCG = round_up_c(TX, 32);      // compute threads of a group (whole warps)
+  static constexpr int NGRP = 1, NC = NGRP * NCG, NT = NC + 32;
   static constexpr size_t SMEM = 128 + 256 + (size_t)NSG * GROUP +
                                  sizeof(T) * ((size_t)NRN * WRC + (size_t)NTT * WTC) + 16 * (NT / 32) + 64;
 };
@@ -991,8 +998,8 @@ struct K2Unit {
       const unsigned char *bz = gb[gback(K, 1)];
       const int mt = mlo + rel - 1;
       T *tm = tt + pmod(K - 1, G::NTT) * G::WTC;
-      tm[0] = tcol<K - 1>(bz, 0, mt);
-      if (lt < G::WTC - TX) tm[TX] = tcol<K - 1>(bz, TX, mt);
+      if (G::NCG <= G::WTC || lt < G::WTC) tm[0] = tcol<K - 1>(bz, 0, mt);
+      if (lt < G::WTC - G::NCG) tm[G::NCG] = tcol<K - 1>(bz, G::NCG, mt);   // columns past the threads
     }
     bool got = true, waited = false;
     // r' on row m over [i0-2R, i0+TX+2R)
@@ -1005,13 +1012,15 @@ struct K2Unit {
       const T *Rr = fld(gb[0], G::OFF_R, I, G::WR), *Qr = fld(gb[0], G::OFF_Q, I, G::WR);
       T *rnm = rn + (K & (G::NRN - 1)) * G::WRC;
       constexpr int k0 = G::HR - 2 * R;
-      T v = Rr[k0];
-      if (kind == K2_ITER) v = fma(-alpha, Qr[k0], v);
-      rnm[0] = v;
-      if (lt < G::WRC - TX) {
-        T v2 = Rr[k0 + TX];
-        if (kind == K2_ITER) v2 = fma(-alpha, Qr[k0 + TX], v2);
-        rnm[TX] = v2;
+      if (G::NCG <= G::WRC || lt < G::WRC) {
+        T v = Rr[k0];
+        if (kind == K2_ITER) v = fma(-alpha, Qr[k0], v);
+        rnm[0] = v;
+      }
+      if (lt < G::WRC - G::NCG) {
+        T v2 = Rr[k0 + G::NCG];
+        if (kind == K2_ITER) v2 = fma(-alpha, Qr[k0 + G::NCG], v2);
+        rnm[G::NCG] = v2;
       }
     }
     if (!compute_sync_and<G::NC>(got)) return false;
@@ -1135,13 +1144,13 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
       const int rsel = (kind == K2_APPLY) ? 0 : st->rsel;
       if (!aborted) {
         K2Unit<T, TX, P, KIND> cx;
-        cx.tid = tid; cx.grp = tid / TX; cx.lt = tid - cx.grp * TX;
+        cx.tid = tid; cx.grp = tid / G::NCG; cx.lt = tid - cx.grp * G::NCG;
         cx.rn = rn + cx.lt; cx.tt = tt + cx.lt; cx.full = rc.full; cx.empty = rc.empty;
         cx.abort = &rc.ctl[CTL_ABORT]; cx.timeout_ns = p.timeout_ns;
         cx.begin(rc.ring, gbase);
         cx.nx = nx; cx.ny = ny; cx.mlo = mlo; cx.j0 = j0; cx.i0 = i0; cx.nr1 = mhi - mlo;
         cx.nrows = rend - j0; cx.ng = ng; cx.pitch = gdp->pitch; cx.col = i0 + cx.lt;
-        cx.col_ok = cx.col < nx;
+        cx.col_ok = cx.lt < TX && cx.col < nx;
         cx.cs.init(cx.col, nx);
         cx.alpha = (kind == K2_ITER) ? (T)st->alpha : (T)0;
         cx.rout = gdp->r[rsel ^ 1]; cx.s_out = gdp->s; cx.zwrap = gdp->zwrap;
@@ -1226,9 +1235,10 @@ __global__ void __launch_bounds__(TX) k_pack(KParams p, const U *user, int which
 // Mixed precision, refinement step: the binary64 residual r (plane r[rsel] of
 // the binary64 grid) scaled by a power of two becomes the binary32 right-hand
 // side b of the inner solve.
-template <int TX>
-__global__ void __launch_bounds__(TX) k_residual_to_f32(const GridDev<double> *g64, const GridDev<float> *g32,
-                                                     const Unit *units, double scale) {
+// (one block of strip-width threads per unit of the binary64 planes)
+static __global__ void k_residual_to_f32(const GridDev<double> *g64, const GridDev<float> *g32, const Unit *units,
+                                  double scale) {
+  const int TX = (int)blockDim.x;
   const Unit un = units[blockIdx.x];
   const GridDev<double> &a = g64[un.g];
   const GridDev<float> &f = g32[un.g];
@@ -1245,9 +1255,10 @@ __global__ void __launch_bounds__(TX) k_residual_to_f32(const GridDev<double> *g
 
 // Mixed precision, refinement step: x += e / scale with e the binary32 inner
 // solution (x plane of the binary32 grid); the update is done in binary64.
-template <int TX>
-__global__ void __launch_bounds__(TX) k_correct_f64(const GridDev<double> *g64, const GridDev<float> *g32,
-                                                  const Unit *units, double inv_scale) {
+// (one block of strip-width threads per unit of the binary64 planes)
+static __global__ void k_correct_f64(const GridDev<double> *g64, const GridDev<float> *g32, const Unit *units,
+                              double inv_scale) {
+  const int TX = (int)blockDim.x;
   const Unit un = units[blockIdx.x];
   const GridDev<double> &a = g64[un.g];
   const GridDev<float> &f = g32[un.g];

@@ -46,7 +46,7 @@ def _csr(P):
 
 
 @pytest.mark.parametrize("spec", GRIDS, ids=[g[0] for g in GRIDS])
-@pytest.mark.parametrize("tiles", [(0, 0), (64, 8), (128, 32)])
+@pytest.mark.parametrize("tiles", [(0, 0), (64, 8), (128, 32), (62, 16)])
 def test_spmv_matches_oracle(spec, tiles):
     pcg = _pcg()
     g = _grid(spec)
@@ -68,14 +68,17 @@ PRECONDS = [(0, 0.0, 0), (1, 0.0, 0), (1, 0.05, 0), (4, 0.0, 0), (3, 0.0, 1), (3
 
 @pytest.mark.parametrize("spec", GRIDS, ids=[g[0] for g in GRIDS])
 @pytest.mark.parametrize("pattern,tau,q", PRECONDS)
-def test_precond_matches_oracle(spec, pattern, tau, q):
+@pytest.mark.parametrize("tile_x", [0, 64])
+def test_precond_matches_oracle(spec, pattern, tau, q, tile_x):
+    """tile_x 0: the default strips (60/62 columns for tril(A^2)/tril(A), whose
+    t phase fills whole warps); 64: strips with a halo pass."""
     pcg = _pcg()
     g = _grid(spec)
     if pattern == 3 and q >= g.nx:
         pytest.skip("band wider than the row")
     P = oracle.OracleProblem.from_grid(g)
     assert P.ainv(pattern, tau, q) == oracle.OK
-    h = pcg.ainv_setup_grid(g, pattern=pattern, drop_tol=tau, band_q=q)
+    h = pcg.ainv_setup_grid(g, pattern=pattern, drop_tol=tau, band_q=q, tile_x=tile_x)
     rng = np.random.default_rng(12)
     r = rng.standard_normal((g.ny, g.nx))
     s = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
