@@ -888,7 +888,9 @@ static int choose_tx(int nx, int elem_size, int pattern) {
 }
 
 // Strip height: about 600 units when the grid allows (the persistent CTAs
-// then take one to a few units each), a multiple of 8 rows in min_ty..64.
+// then take one to a few units each), a multiple of 8 rows in min_ty..64
+// (min_ty itself for small grids: binary64 4, where a short unit keeps the
+// step chain of a single small solve short).
 // A unit costs its height plus the pipeline depth in steps (2 + 2 LD for the
 // preconditioner kernel) and a reduction, which weighs more in the binary32
 // kernels: their strips are 64 rows tall (measured best for single large
@@ -1040,7 +1042,7 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     }
     if (opts->tile_y != 0 && (opts->tile_y < 4 || opts->tile_y > 256)) { set_error("tile_y must be 4..256"); return PCG_EINVAL; }
     h->tx = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 8, opts->pattern);
-    h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx, 8);
+    h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx, 4);
     h->tx32 = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 4, opts->pattern);
     h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32, 64);
     if (!opts->tile_x && !opts->tile_y) {       // shapes tuned earlier in this process win (latency objective)
