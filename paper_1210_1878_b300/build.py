@@ -9,6 +9,7 @@ from __future__ import annotations
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -17,9 +18,10 @@ ROOT = os.path.dirname(HERE)
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["api.cu", "server.cu", "noalloc.cu"]
+CU_SOURCES = ["api.cu", "server.cu", "noalloc.cu", "kernels_f64_64.cu", "kernels_f64_128.cu",
+              "kernels_f32_64.cu", "kernels_f32_128.cu", "kernels_exact.cu"]
 CPP_SOURCES = ["ainv_host.cpp"]
-HEADERS = ["pcg_internal.h", "device.cuh", "kernels.cuh", "handle.cuh"]
+HEADERS = ["pcg_internal.h", "device.cuh", "kernels.cuh", "handle.cuh", "kernel_table.cuh"]
 
 
 def _sources():
@@ -48,6 +50,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             print(" ".join(cmd), file=sys.stderr)
         subprocess.check_call(cmd)
         objs.append(o)
+    cmds = []
     for f in CU_SOURCES:
         o = os.path.join(bdir, f + ".o")
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
@@ -56,8 +59,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
             cmd.insert(1, "-Xptxas=-v")
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
-        subprocess.check_call(cmd)
+        cmds.append(cmd)
         objs.append(o)
+    # the translation units are independent: compile them side by side
+    with ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as pool:
+        for f in [pool.submit(subprocess.check_call, c) for c in cmds]:
+            f.result()
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [NVCC, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", "-rpath=/usr/local/cuda/lib64", "-lpthread"]

@@ -27,76 +27,17 @@ void set_error(const std::string &m) { g_err = m; }
 
 
 // ------------------------------------------------------------ kernel table
-template <typename T, int TX, class P>
-static KernelSet make_set() {
-  KernelSet k;
-  k.k1[K1_ITER] = (const void *)k_stencil<T, TX, K1_ITER>;
-  k.k1[K1_RESID_INIT] = (const void *)k_stencil<T, TX, K1_RESID_INIT>;
-  k.k1[K1_RESID_CHECK] = (const void *)k_stencil<T, TX, K1_RESID_CHECK>;
-  k.k1[K1_SPMV] = (const void *)k_stencil<T, TX, K1_SPMV>;
-  k.k2[K2_ITER] = (const void *)k_precond<T, TX, P, K2_ITER>;
-  k.k2[K2_INIT] = (const void *)k_precond<T, TX, P, K2_INIT>;
-  k.k2[K2_APPLY] = (const void *)k_precond<T, TX, P, K2_APPLY>;
-  k.fin = (const void *)k_finalize<T, TX>;
-  k.pack = (const void *)k_pack<T, double, TX>;
-  k.unpack = (const void *)k_unpack<T, double>;
-  k.smem1 = K1Geom<T, TX>::SMEM;
-  k.smem2 = K2Geom<T, TX, P>::SMEM;
-  k.tx = TX;
-  k.tb = K1Geom<T, TX>::NT;
-  k.rb1 = K1Geom<T, TX>::RB;
-  k.rb2 = K2Geom<T, TX, P>::RB;
-  k.ws = K1Geom<T, TX>::WS; k.we = K1Geom<T, TX>::WE; k.wt = K1Geom<T, TX>::WT;
-  k.wr = K2Geom<T, TX, P>::WR; k.wz = K2Geom<T, TX, P>::WZ;
-  static_assert(K1Geom<T, TX>::NT == K2Geom<T, TX, P>::NT, "both kernels use one block size");
-  k.ok = true;
-  return k;
-}
-
-template <typename T, int TX>
-static KernelSet pick_tx(int pattern, int q) {
-  switch (pattern) {
-    case PCG_PAT_DIAG: return make_set<T, TX, Pat<PCG_PAT_DIAG, 0>>();
-    case PCG_PAT_TRIL_A: return make_set<T, TX, Pat<PCG_PAT_TRIL_A, 0>>();
-    case PCG_PAT_TRIL_A2: return make_set<T, TX, Pat<PCG_PAT_TRIL_A2, 0>>();
-    case PCG_PAT_BAND_T:
-      switch (q) {
-        case 1: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 1>>();
-        case 2: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 2>>();
-        case 3: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 3>>();
-        case 4: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 4>>();
-        case 5: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 5>>();
-        case 6: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 6>>();
-        case 7: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 7>>();
-        case 8: return make_set<T, TX, Pat<PCG_PAT_BAND_T, 8>>();
-        default: break;
-      }
-      break;
-    default: break;
-  }
-  return KernelSet{};
-}
-
-// Strips whose preconditioner t phase (TX + 2R columns) fills whole warps:
-// 64 - 2R columns for binary64, 124 for binary32 (a multiple of 4, for the
-// 16-byte alignment of the tensor tiles), for tril(A) and tril(A^2).
-static int exact_width(int elem_size, int pattern) {
-  if (pattern != PCG_PAT_TRIL_A && pattern != PCG_PAT_TRIL_A2) return 0;
-  if (elem_size == 8) return pattern == PCG_PAT_TRIL_A2 ? 60 : 62;
-  return 124;
-}
-
+// The kernel instantiations live in kernels_*.cu (compiled in parallel).
 template <typename T>
 static KernelSet pick(int tx, int pattern, int q) {
-  if (tx == 64) return pick_tx<T, 64>(pattern, q);
-  if (tx == 128) return pick_tx<T, 128>(pattern, q);
-  if (tx != exact_width((int)sizeof(T), pattern)) return KernelSet{};
   if constexpr (sizeof(T) == 8) {
-    if (tx == 60) return make_set<T, 60, Pat<PCG_PAT_TRIL_A2, 0>>();
-    if (tx == 62) return make_set<T, 62, Pat<PCG_PAT_TRIL_A, 0>>();
+    if (tx == 64) return kernels_f64_64(pattern, q);
+    if (tx == 128) return kernels_f64_128(pattern, q);
+    if (tx == exact_width(8, pattern)) return kernels_f64_exact(tx, pattern);
   } else {
-    if (pattern == PCG_PAT_TRIL_A2) return make_set<T, 124, Pat<PCG_PAT_TRIL_A2, 0>>();
-    return make_set<T, 124, Pat<PCG_PAT_TRIL_A, 0>>();
+    if (tx == 64) return kernels_f32_64(pattern, q);
+    if (tx == 128) return kernels_f32_128(pattern, q);
+    if (tx == exact_width(4, pattern)) return kernels_f32_exact(tx, pattern);
   }
   return KernelSet{};
 }

@@ -33,6 +33,23 @@ struct KernelSet {
   bool ok = false;
 };
 
+// Strips whose preconditioner t phase (TX + 2R columns) fills whole warps:
+// 64 - 2R columns for binary64, 124 for binary32 (a multiple of 4, for the
+// 16-byte alignment of the tensor tiles), for tril(A) and tril(A^2).
+inline int exact_width(int elem_size, int pattern) {
+  if (pattern != PCG_PAT_TRIL_A && pattern != PCG_PAT_TRIL_A2) return 0;
+  if (elem_size == 8) return pattern == PCG_PAT_TRIL_A2 ? 60 : 62;
+  return 124;
+}
+
+// kernel sets per precision and strip width (kernels_*.cu)
+KernelSet kernels_f64_64(int pattern, int q);
+KernelSet kernels_f64_128(int pattern, int q);
+KernelSet kernels_f64_exact(int tx, int pattern);
+KernelSet kernels_f32_64(int pattern, int q);
+KernelSet kernels_f32_128(int pattern, int q);
+KernelSet kernels_f32_exact(int tx, int pattern);
+
 // CTAs of a launch of kernel 1 or 2 over n units: one per unit up to the
 // number resident at once; the CTAs then stride over the units.
 inline int persistent_grid(const KernelSet &k, int which, int n_units) {
