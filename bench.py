@@ -473,6 +473,20 @@ def _kernel_roofline(pcg, h, b, wl, prec, n_wet, zbar, workload):
     return roof
 
 
+def _l2_label(torch, ws_bytes):
+    """Whether one iteration's working set (the algorithmic bytes of the two
+    kernels) streams from HBM or can stay in the L2 between iterations; for an
+    L2-resident grid a fraction of the HBM roofline is not meaningful."""
+    try:
+        l2 = int(torch.cuda.get_device_properties(0).L2_cache_size)
+    except Exception:
+        l2 = 126 * 2 ** 20
+    if ws_bytes > l2:
+        return "inputs larger than L2 (working set ~%.3f GB per iteration vs %d MB L2)" % (ws_bytes / 1e9, l2 >> 20)
+    return ("L2-resident (working set ~%.1f MB per iteration fits the %d MB L2): the HBM fraction "
+            "is not meaningful here" % (ws_bytes / 1e6, l2 >> 20))
+
+
 def max_over_ranks(value, device="cuda"):
     """The maximum of a per-rank float over the process group (the slowest
     rank's time decides a replicated run); the value itself when not
@@ -603,6 +617,7 @@ def main():
     vec_bytes = grid.nx * grid.ny * 8
 
     roof = _kernel_roofline(pcg, h, b, wl, wl["prec"], n_wet, zbar, args.workload)
+    roof["l2_resident"] = _l2_label(torch, n_wet * (4 if wl["prec"] == 1 else 8) * (14 + zbar)).startswith("L2")
 
     # binary64 workloads: the same grid and right-hand side solved in the mixed
     # precision mode (binary32 inner PCG, binary64 refinement; same acceptance
@@ -634,8 +649,7 @@ def main():
                        "iters_per_solve": iters, "outer_per_solve": st.outer_iters,
                        "precision": "binary32 inner / binary64 refinement" if wl["prec"] == 1 else "binary64",
                        "worst_true_relres": worst_true, "setup_s": setup_s,
-                       "l2": "inputs larger than L2 (working set ~%.2f GB vs 126 MB L2)"
-                             % (n_wet * 8 * (14 + zbar) / 1e9),
+                       "l2": _l2_label(torch, n_wet * (4 if wl["prec"] == 1 else 8) * (14 + zbar)),
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes,
                     "d2h_bytes_per_step": vec_bytes},
