@@ -95,9 +95,10 @@ typedef struct {
   int32_t pattern;     /* pcg_pattern */
   double drop_tol;     /* drop |z_mk| sqrt(a_mm / a_kk) < drop_tol after every update; 0 = keep all */
   int32_t band_q;      /* PCG_PAT_BAND_T only: upper bandwidth q, 1..8 */
-  int32_t tile_x;      /* device strip width in points: 64, 128, or the width whose preconditioner pass
-                          fills whole warps (tril(A^2): 60 binary64 / 124 binary32; tril(A): 62 / 124),
-                          valid for the precisions that have it; 0 = chosen per precision */
+  int32_t tile_x;      /* device strip width in points: 64, 128, or a width whose preconditioner pass
+                          fills whole warps (tril(A^2): 60 binary64 / 124 binary32; tril(A): 62 or 124
+                          binary64 / 124 binary32), valid for the precisions that have it; 0 = chosen per
+                          precision (binary64 tril(A): 124 on grids of 2048 columns or more, else 62) */
   int32_t tile_y;      /* device strip height in rows, 4..256; 0 = chosen per precision from nx, ny */
 } ainv_opts;
 
@@ -218,7 +219,7 @@ int pcg_apply_f32(pcg_handle *h, int32_t op, const double *v, double *out, void 
 /* Strip-shape autotuner (batching, tile shapes chosen by measurement): for
  * precision prec (PCG_FP64: the binary64 planes; PCG_MIXED: the binary32
  * planes of the inner iterations) times the two loop kernels of h on strips
- * of 64, 128 or the whole-warp width (tile_x) columns by 8, 16, 32 or 64 rows (ten iterations each, on a
+ * of 64, 128 or the whole-warp widths (tile_x) columns by 8, 16, 32 or 64 rows (ten iterations each, on a
  * right-hand side of ones), rebuilds h's planes with the best shape and
  * returns it in tile_x, tile_y (either may be NULL). objective 0: the
  * shortest kernel time of the grid alone (a single solve); objective 1: the

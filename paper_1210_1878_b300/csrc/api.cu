@@ -34,6 +34,7 @@ static KernelSet pick(int tx, int pattern, int q) {
     if (tx == 64) return kernels_f64_64(pattern, q);
     if (tx == 128) return kernels_f64_128(pattern, q);
     if (tx == exact_width(8, pattern)) return kernels_f64_exact(tx, pattern);
+    if (tx == wide_width(8, pattern)) return kernels_f64_wide(tx, pattern);
   } else {
     if (tx == 64) return kernels_f32_64(pattern, q);
     if (tx == 128) return kernels_f32_128(pattern, q);
@@ -817,12 +818,18 @@ std::string status_name(int s) {
 
 // Strip width. binary64 kernels are bound by the FP64 pipe: narrow strips
 // (more CTAs per SM) whose t phase fills whole warps where the pattern allows
-// (64 - 2R columns). binary32 kernels: of the wide strip (124 or 128 columns)
-// and 64, the one that wastes the fewest columns, ties to the wider strip
-// (fewer halo columns per point).
+// (64 - 2R columns); for tril(A) on grids at least WIDE_MIN_NX columns wide,
+// the 124-column strip. binary32 kernels: of the wide strip (124 or 128
+// columns) and 64, the one that wastes the fewest columns, ties to the wider
+// strip (fewer halo columns per point).
+static constexpr int WIDE_MIN_NX = 2048;
 static int choose_tx(int nx, int elem_size, int pattern) {
   const int ex = exact_width(elem_size, pattern);
-  if (elem_size == 8) return ex ? ex : 64;
+  if (elem_size == 8) {
+    const int wide = wide_width(8, pattern);
+    if (wide && nx >= WIDE_MIN_NX) return wide;
+    return ex ? ex : 64;
+  }
   const int wide = ex ? ex : 128;
   const int ww = (nx + wide - 1) / wide * wide, w64 = (nx + 63) / 64 * 64;
   return (ww - nx <= (w64 - nx) + 16) ? wide : 64;
@@ -976,14 +983,16 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     h->pattern = opts->pattern;
     h->band_q = opts->band_q;
     h->tau = opts->drop_tol;
-    if (opts->tile_x != 0 && opts->tile_x != 64 && opts->tile_x != 128 &&
-        opts->tile_x != exact_width(8, opts->pattern) && opts->tile_x != exact_width(4, opts->pattern)) {
-      set_error("tile_x must be 64, 128 or the whole-warp width of the pattern (60, 62 binary64; 124 binary32)");
+    if (opts->tile_x != 0 && !valid_width(opts->tile_x, opts->pattern)) {
+      set_error("tile_x must be 64, 128 or a whole-warp width of the pattern (tril(A^2): 60 binary64, 124 "
+                "binary32; tril(A): 62 or 124 binary64, 124 binary32)");
       return PCG_EINVAL;
     }
     if (opts->tile_y != 0 && (opts->tile_y < 4 || opts->tile_y > 256)) { set_error("tile_y must be 4..256"); return PCG_EINVAL; }
     h->tx = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 8, opts->pattern);
     h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx, 4);
+    // the wide binary64 strip: 32-row units (measured faster than 64 on 4322 x 3059)
+    if (!opts->tile_y && h->tx == wide_width(8, opts->pattern)) h->ty = std::min(h->ty, 32);
     h->tx32 = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 4, opts->pattern);
     h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32, 64);
     if (!opts->tile_x && !opts->tile_y) {       // shapes tuned earlier in this process win (latency objective)
@@ -1225,7 +1234,8 @@ int pcg_autotune(pcg_handle *h, int32_t prec, int32_t objective, int32_t *tile_x
     double best = 1e300;
     int last_ty = -1;
     const int ex = exact_width(prec == PCG_MIXED ? 4 : 8, h->pattern);
-    for (int cx : {64, 128, ex}) {
+    const int wide = prec == PCG_MIXED ? 0 : wide_width(8, h->pattern);
+    for (int cx : {64, 128, ex, wide}) {
       if (cx == 0) continue;
       last_ty = -1;
       for (int cy : {8, 16, 32, 64}) {

@@ -41,11 +41,24 @@ inline int exact_width(int elem_size, int pattern) {
   if (elem_size == 8) return pattern == PCG_PAT_TRIL_A2 ? 60 : 62;
   return 124;
 }
+// A wider binary64 strip for tril(A): 124 columns, whose r' pass is 128
+// columns (4 whole warps) and whose t pass is 126; its ring is small enough
+// for 5 CTAs per SM, and on wide grids it beats two 62-column strips (fewer
+// halo columns per point). tril(A^2)'s ring at this width leaves 3 CTAs per
+// SM, which is slower than 60.
+inline int wide_width(int elem_size, int pattern) {
+  return (elem_size == 8 && pattern == PCG_PAT_TRIL_A) ? 124 : 0;
+}
+inline bool valid_width(int tx, int pattern) {
+  return tx == 64 || tx == 128 || tx == exact_width(8, pattern) || tx == exact_width(4, pattern) ||
+         tx == wide_width(8, pattern);
+}
 
 // kernel sets per precision and strip width (kernels_*.cu)
 KernelSet kernels_f64_64(int pattern, int q);
 KernelSet kernels_f64_128(int pattern, int q);
 KernelSet kernels_f64_exact(int tx, int pattern);
+KernelSet kernels_f64_wide(int tx, int pattern);
 KernelSet kernels_f32_64(int pattern, int q);
 KernelSet kernels_f32_128(int pattern, int q);
 KernelSet kernels_f32_exact(int tx, int pattern);

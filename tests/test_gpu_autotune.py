@@ -64,3 +64,17 @@ def test_autotune_throughput_objective():
     with pytest.raises(pcg.PCGError) as e:
         pcg.pcg_autotune(h, 1, objective=2)
     assert e.value.status == pcg.PCG_EINVAL
+
+
+def test_autotune_fp64_trilA_offers_both_whole_warp_widths():
+    """binary64 tril(A) has two whole-warp strips (62 and 124 columns) besides
+    64 and 128; the tuned one is among them and solves correctly."""
+    import paper_1210_1878_b300 as pcg
+    cfg = dict(nx=260, ny=53, land=0.3)
+    g = gridgen.make_grid(seed=gridgen.seed_for(8), **cfg)
+    h = pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A)
+    assert pcg.pcg_tiles(h, 0)[0] == 62            # narrow grid: the 62-column strip by default
+    tx, ty = pcg.pcg_autotune(h, 0)
+    assert tx in (62, 64, 124, 128) and ty in (8, 16, 32, 64)
+    assert pcg.pcg_tiles(h, 0) == (tx, ty)
+    _check_solve(pcg, h, g, 0)

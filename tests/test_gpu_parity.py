@@ -46,7 +46,7 @@ def _csr(P):
 
 
 @pytest.mark.parametrize("spec", GRIDS, ids=[g[0] for g in GRIDS])
-@pytest.mark.parametrize("tiles", [(0, 0), (64, 8), (128, 32), (62, 16)])
+@pytest.mark.parametrize("tiles", [(0, 0), (64, 8), (128, 32), (62, 16), (124, 16)])
 def test_spmv_matches_oracle(spec, tiles):
     pcg = _pcg()
     g = _grid(spec)
@@ -68,12 +68,15 @@ PRECONDS = [(0, 0.0, 0), (1, 0.0, 0), (1, 0.05, 0), (4, 0.0, 0), (3, 0.0, 1), (3
 
 @pytest.mark.parametrize("spec", GRIDS, ids=[g[0] for g in GRIDS])
 @pytest.mark.parametrize("pattern,tau,q", PRECONDS)
-@pytest.mark.parametrize("tile_x", [0, 64])
+@pytest.mark.parametrize("tile_x", [0, 64, 124])
 def test_precond_matches_oracle(spec, pattern, tau, q, tile_x):
     """tile_x 0: the default strips (60/62 columns for tril(A^2)/tril(A), whose
-    t phase fills whole warps); 64: strips with a halo pass."""
+    t phase fills whole warps); 64: strips with a halo pass; 124: the wide
+    binary64 strip of tril(A)."""
     pcg = _pcg()
     g = _grid(spec)
+    if tile_x == 124 and pattern != pcg.PCG_PAT_TRIL_A:
+        pytest.skip("124-column binary64 strips exist for tril(A) only")
     if pattern == 3 and q >= g.nx:
         pytest.skip("band wider than the row")
     P = oracle.OracleProblem.from_grid(g)
@@ -99,18 +102,19 @@ def _tight_reference(P, b):
 
 
 SOLVES = [
-    ("tiny-trilA", dict(gridgen.TINY), 0, 0, 0.0, 0),
-    ("tiny-trilA2", dict(gridgen.TINY), 0, 1, 0.0, 0),
-    ("coarse-trilA2", dict(gridgen.COARSE), 1, 1, 0.05, 0),
-    ("coarse-jacobi", dict(gridgen.COARSE), 1, 4, 0.0, 0),
-    ("coarse-bandT4", dict(gridgen.COARSE), 1, 3, 0.0, 4),
-    ("ragged-trilA", dict(nx=203, ny=77, land=0.3), 7, 0, 0.0, 0),
-    ("orca025-trilA2", dict(gridgen.ORCA025), 2, 1, 0.05, 0),
+    ("tiny-trilA", dict(gridgen.TINY), 0, 0, 0.0, 0, 0),
+    ("tiny-trilA2", dict(gridgen.TINY), 0, 1, 0.0, 0, 0),
+    ("coarse-trilA2", dict(gridgen.COARSE), 1, 1, 0.05, 0, 0),
+    ("coarse-jacobi", dict(gridgen.COARSE), 1, 4, 0.0, 0, 0),
+    ("coarse-bandT4", dict(gridgen.COARSE), 1, 3, 0.0, 4, 0),
+    ("ragged-trilA", dict(nx=203, ny=77, land=0.3), 7, 0, 0.0, 0, 0),
+    ("ragged-trilA-wide", dict(nx=203, ny=77, land=0.3), 7, 0, 0.0, 0, 124),   # 124-column strips
+    ("orca025-trilA2", dict(gridgen.ORCA025), 2, 1, 0.05, 0, 0),
 ]
 
 
-@pytest.mark.parametrize("name,cfg,ci,pattern,tau,q", SOLVES, ids=[s[0] for s in SOLVES])
-def test_solve_matches_oracle(name, cfg, ci, pattern, tau, q):
+@pytest.mark.parametrize("name,cfg,ci,pattern,tau,q,tile_x", SOLVES, ids=[s[0] for s in SOLVES])
+def test_solve_matches_oracle(name, cfg, ci, pattern, tau, q, tile_x):
     pcg = _pcg()
     g = gridgen.make_grid(seed=gridgen.seed_for(ci), **cfg)
     P = oracle.OracleProblem.from_grid(g)
@@ -118,7 +122,9 @@ def test_solve_matches_oracle(name, cfg, ci, pattern, tau, q):
     b = P.to_wet(g.b)
     ref = P.pcg(b, rtol=1e-10)
     assert ref.status == oracle.OK
-    h = pcg.ainv_setup_grid(g, pattern=pattern, drop_tol=tau, band_q=q)
+    h = pcg.ainv_setup_grid(g, pattern=pattern, drop_tol=tau, band_q=q, tile_x=tile_x, tile_y=8 if tile_x else 0)
+    if tile_x:
+        assert pcg.pcg_tiles(h) == (tile_x, 8)
     x = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
     st = pcg.pcg_solve(h, _dev(g.b), x, pcg.make_opts(rtol=1e-10))
     assert st.status == pcg.PCG_OK
