@@ -72,6 +72,12 @@ def test_pattern_invariants(pattern, q, tau):
         assert np.all(np.abs(Z[m_idx, k_idx]) * np.sqrt(a[m_idx] / a[k_idx]) >= tau)
     if pattern == oracle.PAT_TRIL_A2 and tau == 0.3:
         assert np.count_nonzero(np.triu(Z, 1)) < np.count_nonzero(np.triu(allowed, 1))
+    if tau == 0 and pattern == oracle.PAT_TRIL_A:
+        # M-matrix, connected rows: with nothing dropped Z fills the structure of tril(A)
+        assert np.array_equal(Z != 0, allowed)
+    if tau == 0 and pattern == oracle.PAT_TRIL_A2:
+        # two-step couplings (WW, SS, SW, SE) are filled, beyond tril(A)
+        assert np.count_nonzero((Z != 0) & ~_lower_structure(A, 1)) > Z.shape[0]
 
 
 def _path_grid(n, c=1.0, s_end=1.0, s_mid=0.0, cvar=None):
@@ -86,6 +92,25 @@ def _path_grid(n, c=1.0, s_end=1.0, s_mid=0.0, cvar=None):
     sh = np.full((1, nx), s_mid)
     sh[0, 0] = sh[0, n - 1] = s_end
     return oracle.OracleProblem(nx, 1, wet, ce, cn, sh)
+
+
+def test_drop_rule_hand_computed():
+    """Right-looking construction with drops after each update (Section 3),
+    worked by hand on three wet cells in a row, A = tridiag(-1; 2, 5, 2):
+    i = 1 gives z_12 = 1/2 with scaled size (1/2) sqrt(2/5) = 0.316; i = 2 then
+    has d_2 = 5 - 1/2 (or 5 if z_12 was dropped) and z_23 = 1/d_2 with scaled
+    size z_23 sqrt(5/2); d_3 = 2 - z_23. At tau = 0.4 both entries drop; at
+    tau = 0.3 both stay (0.316 and 0.351), so Z and D are the values below.
+    An unscaled or inversely scaled test keeps z_12 at 0.4 or drops z_23 at 0.3."""
+    P = _path_grid(3, c=1.0, s_end=1.0, s_mid=3.0)
+    assert np.array_equal(np.diag(P.dense()), [2.0, 5.0, 2.0])
+    assert P.ainv(oracle.PAT_TRIL_A, 0.4) == oracle.OK
+    Z, d = P.z_dense()
+    assert np.array_equal(Z, np.eye(3)) and np.array_equal(d, [2.0, 5.0, 2.0])
+    assert P.ainv(oracle.PAT_TRIL_A, 0.3) == oracle.OK
+    Z, d = P.z_dense()
+    Zh = np.array([[1.0, 0.5, 0.0], [0.0, 1.0, 2.0 / 9.0], [0.0, 0.0, 1.0]])
+    assert np.allclose(Z, Zh, rtol=1e-15, atol=0) and np.allclose(d, [2.0, 4.5, 16.0 / 9.0], rtol=1e-15, atol=0)
 
 
 def _cholesky_upper_tridiag(T):
