@@ -45,7 +45,7 @@ def _csr(P):
 
 
 @pytest.mark.parametrize("spec", GRIDS, ids=[g[0] for g in GRIDS])
-@pytest.mark.parametrize("tiles", [(0, 0), (64, 8), (128, 32)])
+@pytest.mark.parametrize("tiles", [(0, 0), (64, 8), (128, 32), (0, 4)])
 def test_spmv_f32_matches_oracle(spec, tiles):
     import paper_1210_1878_b300 as pcg
     g = _grid(spec)
@@ -70,14 +70,15 @@ PRECONDS = [(0, 0.0, 0), (1, 0.0, 0), (1, 0.05, 0), (4, 0.0, 0), (3, 0.0, 1), (3
 
 @pytest.mark.parametrize("spec", GRIDS, ids=[g[0] for g in GRIDS])
 @pytest.mark.parametrize("pattern,tau,q", PRECONDS)
-def test_precond_f32_matches_oracle(spec, pattern, tau, q):
+@pytest.mark.parametrize("ty", [0, 4])
+def test_precond_f32_matches_oracle(spec, pattern, tau, q, ty):
     import paper_1210_1878_b300 as pcg
     g = _grid(spec)
     if pattern == 3 and q >= g.nx:
         pytest.skip("band wider than the row")
     P = oracle.OracleProblem.from_grid(g)
     assert P.ainv(pattern, tau, q) == oracle.OK
-    h = pcg.ainv_setup_grid(g, pattern=pattern, drop_tol=tau, band_q=q)
+    h = pcg.ainv_setup_grid(g, pattern=pattern, drop_tol=tau, band_q=q, tile_y=ty)
     rng = np.random.default_rng(22)
     r = rng.standard_normal((g.ny, g.nx))
     s = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
