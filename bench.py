@@ -197,16 +197,17 @@ def run_reference(args, wl_name, wl):
     return 0
 
 
-def _traffic_record(kernel_key):
+def _traffic_record(kernel_key, tiles):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the
-    current kernel source (profiles/traffic.txt: key bytes source_sha)."""
+    current kernel source and strip shape (profiles/traffic.txt: key bytes
+    source_sha tiles)."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     src = os.path.join(ROOT, "paper_1210_1878_b300", "csrc", "kernels.cuh")
     try:
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         for line in open(path):
             p = line.split()
-            if len(p) >= 3 and p[0] == kernel_key and p[2] == sha:
+            if len(p) >= 4 and p[0] == kernel_key and p[2] == sha and p[3] == tiles:
                 return float(p[1])
     except Exception:
         pass
@@ -455,7 +456,8 @@ def _kernel_roofline(pcg, h, b, wl, prec, n_wet, zbar, workload):
     t_hbm = by / (hbm_peak * 1e9)
     t_alu = fl / (FP64_PEAK_TFLOPS * 1e12)
     kname = dom + ("<float>" if mixed else "<double>")
-    traffic = _traffic_record(f"{kname}:{workload}")
+    tiles = "%dx%d" % pcg.pcg_tiles(h, prec)
+    traffic = _traffic_record(f"{kname}:{workload}", tiles)
     if t_alu > t_hbm:
         roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": tflops / FP64_PEAK_TFLOPS, "traffic": traffic,
@@ -466,7 +468,7 @@ def _kernel_roofline(pcg, h, b, wl, prec, n_wet, zbar, workload):
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "traffic": traffic, "peak_kind": peak_kind}
     it_bytes = bytes_k1 + bytes_k2
-    roof.update({"kernel": kname, "ms_per_launch": ms_dom, "alg_bytes_per_launch": by,
+    roof.update({"kernel": kname, "tiles": tiles, "ms_per_launch": ms_dom, "alg_bytes_per_launch": by,
                  "per_iteration": {"ms_stencil": ms_k1, "ms_precond": ms_k2, "alg_bytes": it_bytes,
                                    "alg_gbs": it_bytes / ((ms_k1 + ms_k2) * 1e-3) / 1e9,
                                    "hbm_frac": it_bytes / ((ms_k1 + ms_k2) * 1e-3) / 1e9 / hbm_peak}})
@@ -581,7 +583,8 @@ def main():
     b = torch.from_numpy(grid.b).cuda()
     x = torch.zeros_like(b)
     if args.kernels_only:
-        print(pcg.pcg_profile_kernels(h, b, iters=3, prec=wl["prec"]))
+        ms = pcg.pcg_profile_kernels(h, b, iters=3, prec=wl["prec"])
+        print(json.dumps({"ms_stencil": ms[0], "ms_precond": ms[1], "tiles": "%dx%d" % pcg.pcg_tiles(h, wl["prec"])}))
         h.close()
         return 0
     zbar = _z_offdiag_per_wet(pcg, h)
