@@ -99,7 +99,9 @@ typedef struct {
                           fills whole warps (tril(A^2): 60 binary64 / 124 binary32; tril(A): 62 or 124
                           binary64 / 124 binary32), valid for the precisions that have it; 0 = chosen per
                           precision (binary64 tril(A): 124 on grids of 2048 columns or more, else 62) */
-  int32_t tile_y;      /* device strip height in rows, 4..256; 0 = chosen per precision from nx, ny */
+  int32_t tile_y;      /* device strip height in rows, 4..256; 0 = chosen per precision at setup: the height
+                          (4..128) minimising a model of the two loop launches' slowest CTA / SM over the
+                          grid's wet strips and the resident CTAs (a shape tuned earlier wins) */
 } ainv_opts;
 
 typedef enum { PCG_FP64 = 0, PCG_MIXED = 1 } pcg_precision;
