@@ -846,31 +846,31 @@ static int choose_ty(int nx, int ny, int tx, int min_ty) {
 // Strip height: the candidate that minimises a makespan model of one
 // iteration's two persistent launches over the grid's active units. CTA c of
 // a launch with G resident CTAs takes units c, c + G, ... (band-major order,
-// as upload_planes builds them); a unit of h rows costs h + 3 steps in
-// k_stencil and h + 2 LD + 2 in k_precond (its pipeline depth). k_precond's
-// time follows its slowest CTA; k_stencil's (more CTAs per SM, which share
-// the SM) follows its slowest SM, CTA c taken to be on SM c mod nsm, divided
-// by the CTAs per SM; a k_precond step weighs 1.5 k_stencil steps. Few units
-// (small grids) make every CTA's chain one short unit; many units make the
-// count per CTA, and its rounding, decide. Measured on 4322 x 3059,
-// 1442 x 1021, 722 x 511 and 182 x 149 grids in both precisions, the model's
-// height was the fastest of 6 to 9 heights tried (up to 2.7x faster than a
-// fixed 64 rows for binary32 on small grids).
-static int model_ty(const HostGrid &G, int tx, const KernelSet &ks, int ld, int nsm) {
+// as upload_planes builds them); a launch lasts as long as its slowest CTA's
+// chain of steps. A unit of h rows costs h + 3 steps in k_stencil and
+// h + 2 LD + 2 in k_precond (the pipeline depths) plus UNIT_STEPS for its
+// reduction and the refill of the stream; a k_precond step weighs 1.5
+// k_stencil steps. Few units (small grids) make every CTA's chain one short
+// unit; many units make the count per CTA, and its rounding, decide.
+// Measured on 4322 x 3059 (three strip / precision pairs, 7 to 9 heights
+// each), 1442 x 1021, 722 x 511 and 182 x 149 (both precisions, 7 heights),
+// the model's height was the fastest one every time (up to 2.7x faster than
+// a fixed 64 rows for binary32 on small grids).
+static int model_ty(const HostGrid &G, int tx, const KernelSet &ks, int ld) {
+  constexpr double UNIT_STEPS = 10.0;
   static const int cand[] = {4, 8, 16, 24, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128};
   const int ntx = (G.nx + tx - 1) / tx;
   std::vector<uint8_t> row_wet((size_t)ntx * G.ny, 0);     // [strip][row]: any wet cell
   for (int j = 0; j < G.ny; ++j)
     for (int i = 0; i < G.nx; ++i)
       if (G.idx[(size_t)j * G.nx + i] >= 0) row_wet[(size_t)(i / tx) * G.ny + j] = 1;
-  const int g1 = std::max(ks.ctas1, 1), g2 = std::max(ks.ctas2, 1), per_sm1 = std::max(1, g1 / std::max(nsm, 1));
-  std::vector<double> c1(g1), c2(g2), sm1(std::max(nsm, 1));
+  const int g1 = std::max(ks.ctas1, 1), g2 = std::max(ks.ctas2, 1);
+  std::vector<double> c1(g1), c2(g2);
   int best_ty = cand[0];
   double best = 1e300;
   for (int ty : cand) {
     std::fill(c1.begin(), c1.end(), 0.0);
     std::fill(c2.begin(), c2.end(), 0.0);
-    std::fill(sm1.begin(), sm1.end(), 0.0);
     long k = 0;
     const int nty = (G.ny + ty - 1) / ty;
     for (int sy = 0; sy < nty; ++sy) {
@@ -879,14 +879,12 @@ static int model_ty(const HostGrid &G, int tx, const KernelSet &ks, int ld, int 
         bool any = false;
         for (int j = j0; j < j1 && !any; ++j) any = row_wet[(size_t)sx * G.ny + j] != 0;
         if (!any) continue;
-        c1[k % g1] += (j1 - j0) + 3;
-        c2[k % g2] += (j1 - j0) + 2 * ld + 2;
+        c1[k % g1] += (j1 - j0) + 3 + UNIT_STEPS;
+        c2[k % g2] += (j1 - j0) + 2 * ld + 2 + UNIT_STEPS;
         ++k;
       }
     }
-    for (int c = 0; c < g1; ++c) sm1[c % sm1.size()] += c1[c];
-    const double cost = *std::max_element(sm1.begin(), sm1.end()) / per_sm1 +
-                        1.5 * *std::max_element(c2.begin(), c2.end());
+    const double cost = *std::max_element(c1.begin(), c1.end()) + 1.5 * *std::max_element(c2.begin(), c2.end());
     if (cost < best) { best = cost; best_ty = ty; }
     if (ty >= G.ny) break;                             // taller strips give the same units
   }
@@ -1038,14 +1036,11 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx, 4);
     h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32, 64);
     if (!opts->tile_y) {                        // heights from the makespan model where the kernels exist
-      int dev = 0, nsm = 0;
-      CK(cudaGetDevice(&dev));
-      CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
       const int ld = opts->pattern == PCG_PAT_TRIL_A2 ? 2 : (opts->pattern == PCG_PAT_TRIL_A ? 1 : 0);
       KernelSet k64 = pick<double>(h->tx, opts->pattern, opts->band_q);
-      if (k64.ok && prepare_set(k64) == PCG_OK) h->ty = model_ty(h->G, h->tx, k64, ld, nsm);
+      if (k64.ok && prepare_set(k64) == PCG_OK) h->ty = model_ty(h->G, h->tx, k64, ld);
       KernelSet k32 = pick<float>(h->tx32, opts->pattern, opts->band_q);
-      if (k32.ok && prepare_set(k32) == PCG_OK) h->ty32 = model_ty(h->G, h->tx32, k32, ld, nsm);
+      if (k32.ok && prepare_set(k32) == PCG_OK) h->ty32 = model_ty(h->G, h->tx32, k32, ld);
     }
     if (!opts->tile_x && !opts->tile_y) {       // shapes tuned earlier in this process win (latency objective)
       tuned_shape(grid->nx, grid->ny, opts->pattern, opts->band_q, PCG_FP64, 0, &h->tx, &h->ty);
