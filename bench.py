@@ -468,6 +468,10 @@ def _kernel_roofline(pcg, h, b, wl, prec, n_wet, zbar, workload):
         roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                 "traffic": traffic, "peak_kind": peak_kind}
     it_bytes = bytes_k1 + bytes_k2
+    if traffic is not None:
+        # the ncu DRAM bytes of one launch over the live launch time
+        roof["dram_gbs"] = traffic / (ms_dom * 1e-3) / 1e9
+        roof["dram_frac"] = roof["dram_gbs"] / hbm_peak
     roof.update({"kernel": kname, "tiles": tiles, "ms_per_launch": ms_dom, "alg_bytes_per_launch": by,
                  "per_iteration": {"ms_stencil": ms_k1, "ms_precond": ms_k2, "alg_bytes": it_bytes,
                                    "alg_gbs": it_bytes / ((ms_k1 + ms_k2) * 1e-3) / 1e9,
