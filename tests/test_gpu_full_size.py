@@ -96,3 +96,25 @@ def test_full_size_solve(full, pattern, prec, key):
     true_rel = np.linalg.norm(bw - P.spmv(P.to_wet(xg))) / np.linalg.norm(bw)
     assert true_rel <= 1e-10 * (1 + 1e-3), true_rel
     assert abs(st.true_relres - true_rel) <= 1e-3 * 1e-10 + 1e-3 * true_rel
+
+
+def test_full_size_f32_kernels(full):
+    """The binary32 kernels of the mixed mode (its default strips) at full size,
+    element by element: bound 32 u (u = 2^-24) of the absolute-value products,
+    as in the smaller binary32 parity tests."""
+    pcg, g, P, hs = full
+    assert P.ainv(oracle.PAT_TRIL_A2, 0.05, 0) == oracle.OK
+    tol = 32 * 2.0 ** -24
+    rng = np.random.default_rng(33)
+    v = rng.standard_normal((g.ny, g.nx))
+    out = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
+    pcg.pcg_apply_f32(hs[1], 0, torch.from_numpy(v).cuda(), out)
+    vw = P.to_wet(v)
+    err = np.abs(P.to_wet(out.cpu().numpy()) - P.spmv(vw))
+    assert np.all(err <= tol * (abs(_csr(P)) @ np.abs(vw)) + 1e-300)
+    pcg.pcg_apply_f32(hs[1], 1, torch.from_numpy(v).cuda(), out)
+    cp, row, val, d = P.z()
+    Z = sp.csc_matrix((np.abs(val), row, cp), shape=(P.n, P.n))
+    err = np.abs(P.to_wet(out.cpu().numpy()) - P.apply(vw))
+    assert np.all(err <= tol * (Z @ ((Z.T @ np.abs(vw)) / d)) + 1e-300)
+    assert pcg.pcg_tiles(hs[1], 1)[0] == 124
