@@ -1031,8 +1031,12 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
       return PCG_EINVAL;
     }
     if (opts->tile_y != 0 && (opts->tile_y < 4 || opts->tile_y > 256)) { set_error("tile_y must be 4..256"); return PCG_EINVAL; }
-    h->tx = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 8, opts->pattern);
-    h->tx32 = opts->tile_x ? opts->tile_x : choose_tx(grid->nx, 4, opts->pattern);
+    // an explicit width applies to the precisions that have kernels for it; the
+    // other precision keeps its default width
+    const bool x64 = opts->tile_x && pick<double>(opts->tile_x, opts->pattern, opts->band_q).ok;
+    const bool x32 = opts->tile_x && pick<float>(opts->tile_x, opts->pattern, opts->band_q).ok;
+    h->tx = x64 ? opts->tile_x : choose_tx(grid->nx, 8, opts->pattern);
+    h->tx32 = x32 ? opts->tile_x : choose_tx(grid->nx, 4, opts->pattern);
     h->ty = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx, 4);
     h->ty32 = opts->tile_y ? opts->tile_y : choose_ty(grid->nx, grid->ny, h->tx32, 64);
     if (!opts->tile_y) {                        // heights from the makespan model where the kernels exist

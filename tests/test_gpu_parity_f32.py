@@ -101,3 +101,23 @@ def test_apply_f32_rejects_bad_op():
     with pytest.raises(pcg.PCGError) as e:
         pcg.pcg_apply_f32(h, 2, v, v)
     assert e.value.status == pcg.PCG_EINVAL
+
+
+def test_explicit_width_applies_to_the_precisions_that_have_it():
+    """tile_x = 124 with tril(A^2): binary32 kernels exist for it, binary64 ones
+    do not (binary64 keeps its default 60-column strips); both paths solve."""
+    import paper_1210_1878_b300 as pcg
+    g = _grid(GRIDS[2])
+    P = oracle.OracleProblem.from_grid(g)
+    h = pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A2, drop_tol=0.05, tile_x=124, tile_y=16)
+    assert pcg.pcg_tiles(h, 0) == (60, 16)
+    for prec in (0, 1):
+        x = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
+        st = pcg.pcg_solve(h, torch.from_numpy(g.b).cuda(), x, pcg.make_opts(rtol=1e-10, prec=prec))
+        assert st.status == pcg.PCG_OK
+        bw = P.to_wet(g.b)
+        assert np.linalg.norm(bw - P.spmv(P.to_wet(x.cpu().numpy()))) / np.linalg.norm(bw) <= 1e-10 * (1 + 1e-3)
+    assert pcg.pcg_tiles(h, 1) == (124, 16)
+    with pytest.raises(pcg.PCGError) as e:
+        pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A2, tile_x=100)
+    assert e.value.status == pcg.PCG_EINVAL
