@@ -501,9 +501,11 @@ struct K1Geom {
                        OFF_A = OFF_E + fb(WE), OFF_X = OFF_A + fb(WT), GROUP = OFF_X + fb(WT);   // bytes
   // group slots: the groups a step reads (rows m-3..m) plus at least one in
   // flight. The binary32 kernel is bound by its compute warps, so its ring is
-  // kept small (about 40 KB) for CTAs per SM.
+  // kept small (about 40 KB) for CTAs per SM. binary64: 8 rows (4 in flight);
+  // strips wider than 64 columns keep 5 (1 in flight), which lets 6 CTAs
+  // instead of 4 share an SM (measured faster on 124-column strips).
   static constexpr int LIVE = (3 + RB - 1) / RB + 1;
-  static constexpr int NSG = RB == 1 ? 8 : ring_groups(40000, GROUP, LIVE);
+  static constexpr int NSG = RB == 1 ? (TX > 64 ? 5 : 8) : ring_groups(40000, GROUP, LIVE);
   // NGRP warp groups of TX compute threads (with 2, each step's work is split:
   // group 0 d', the x update and the waits, group 1 q = A d' and its stores;
   // measured no faster than 1 on this GPU), then the producer warp
