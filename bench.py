@@ -482,15 +482,19 @@ def _kernel_roofline(pcg, h, b, wl, prec, n_wet, zbar, workload):
 def _l2_label(torch, ws_bytes):
     """Whether one iteration's working set (the algorithmic bytes of the two
     kernels) streams from HBM or can stay in the L2 between iterations; for an
-    L2-resident grid a fraction of the HBM roofline is not meaningful."""
+    L2-resident grid a fraction of the HBM roofline is not meaningful. The L2
+    is split between the GPU's two dies: an 82 MB working set (1442 x 1021,
+    binary32) still hit the L2 only 51-54 % of the time (ncu, warm caches), so
+    half the L2 is the bound used here."""
     try:
         l2 = int(torch.cuda.get_device_properties(0).L2_cache_size)
     except Exception:
         l2 = 126 * 2 ** 20
-    if ws_bytes > l2:
-        return "inputs larger than L2 (working set ~%.3f GB per iteration vs %d MB L2)" % (ws_bytes / 1e9, l2 >> 20)
-    return ("L2-resident (working set ~%.1f MB per iteration fits the %d MB L2): the HBM fraction "
-            "is not meaningful here" % (ws_bytes / 1e6, l2 >> 20))
+    if ws_bytes > l2 // 2:
+        return ("streams from HBM (working set ~%.3f GB per iteration vs %d MB L2, %d MB per die)"
+                % (ws_bytes / 1e9, l2 >> 20, l2 >> 21))
+    return ("L2-resident (working set ~%.1f MB per iteration within one die's %d MB of L2): the HBM "
+            "fraction is not meaningful here" % (ws_bytes / 1e6, l2 >> 21))
 
 
 def max_over_ranks(value, device="cuda"):
