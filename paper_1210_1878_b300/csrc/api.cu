@@ -151,6 +151,10 @@ static int upload_planes(pcg_handle *h, DevPlanes<T> &P, cudaStream_t s) {
   P.ty = sizeof(T) == 4 ? h->ty32 : h->ty;
   P.gx = 128 / (int)sizeof(T);
   const int ntx = (G.nx + P.tx - 1) / P.tx;
+  if (ntx > INT16_MAX || (G.ny + P.ty - 1) / P.ty > INT16_MAX) {   // strip coordinates are 16-bit
+    set_error("more than 32767 strips in one direction: use wider (tile_x) or taller (tile_y) strips");
+    return PCG_EINVAL;
+  }
   P.pitch = (int)elem_round((size_t)P.gx + (size_t)ntx * P.tx + P.gx, 128 / sizeof(T));
   P.nz = F.slots.n; P.nw = F.slots.n_wrap;
   P.plane_elems = (size_t)(G.ny + 2 * GY) * P.pitch;
@@ -432,6 +436,7 @@ int plan_single(pcg_handle *h) {
 template <typename T>
 static int plan_build_t(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls,
                         DevPlanes<T> pcg_handle::*planes, cudaStream_t s) {
+  if (n > INT16_MAX) { set_error("more than 32767 grids in one plan"); return PCG_EINVAL; }   // 16-bit grid index
   L.ls = ls;
   std::vector<std::vector<int>> groups;
   for (int i = 0; i < n; ++i) {
@@ -866,9 +871,10 @@ static int model_ty(const HostGrid &G, int tx, const KernelSet &ks, int ld) {
       if (G.idx[(size_t)j * G.nx + i] >= 0) row_wet[(size_t)(i / tx) * G.ny + j] = 1;
   const int g1 = std::max(ks.ctas1, 1), g2 = std::max(ks.ctas2, 1);
   std::vector<double> c1(g1), c2(g2);
-  int best_ty = cand[0];
+  int best_ty = 128;
   double best = 1e300;
   for (int ty : cand) {
+    if ((G.ny + ty - 1) / ty > INT16_MAX) continue;    // strip coordinates are 16-bit
     std::fill(c1.begin(), c1.end(), 0.0);
     std::fill(c2.begin(), c2.end(), 0.0);
     long k = 0;

@@ -209,3 +209,22 @@ def test_bounded_wait_reports_timeout():
     x = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
     st = pcg.pcg_solve(h, _dev(g.b), x)
     assert st.status == pcg.PCG_OK and st.true_relres <= 1e-10
+
+
+def test_strip_counts_beyond_16_bits_are_refused():
+    """Strip coordinates are 16-bit: a grid 140000 rows tall cannot take 4-row
+    strips (35000 of them); the default height keeps the count in range and the
+    solve still passes the acceptance test."""
+    pcg = _pcg()
+    g = gridgen.make_grid(seed=gridgen.seed_for(0) + 900, nx=5, ny=140000, land=0.2)
+    with pytest.raises(pcg.PCGError) as e:
+        pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A, tile_y=4)
+    assert e.value.status == pcg.PCG_EINVAL
+    h = pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A)
+    assert (g.ny + pcg.pcg_tiles(h)[1] - 1) // pcg.pcg_tiles(h)[1] <= 32767
+    P = oracle.OracleProblem.from_grid(g)
+    x = torch.zeros((g.ny, g.nx), dtype=torch.float64, device="cuda")
+    st = pcg.pcg_solve(h, _dev(g.b), x, pcg.make_opts(rtol=1e-10, max_iter=5000))
+    assert st.status == pcg.PCG_OK
+    bw = P.to_wet(g.b)
+    assert np.linalg.norm(bw - P.spmv(P.to_wet(x.cpu().numpy()))) / np.linalg.norm(bw) <= 1e-10 * (1 + 1e-3)
