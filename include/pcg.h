@@ -161,14 +161,16 @@ int pcg_solve(pcg_handle *h, const double *b, double *x, const pcg_opts *opts, p
 int pcg_solve_batched(pcg_handle *const *hs, int32_t nbatch, const double *const *b, double *const *x,
                       const pcg_opts *opts, pcg_stats *stats, void *cuda_stream);
 
-/* q = A v on the device kernels of the iteration (Section 3, Eq. 9). */
+/* q = A v on the device kernels of the iteration (Section 3, Eq. 9).
+ * Returns PCG_OK, PCG_EINVAL, PCG_ECUDA, or PCG_ETIMEOUT when a bounded device
+ * wait gave up (q is then incomplete). */
 int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream);
 
 /* q = A v like pcg_spmv, but without allocating anything. The paper has no
- * counterpart: this entry point exists for callers that cannot allocate
- * device memory where they call it -- an ocean model whose own memory
- * manager owns the whole device, or code running while an allocation would
- * break its contract (inside a stream capture, or under a fixed memory budget).
+ * counterpart: this entry point exists for callers that cannot let a library
+ * allocate device memory where they call it -- an ocean model whose own memory
+ * manager claims the whole device at start-up, or code that runs under a fixed
+ * device-memory budget that a hidden cudaMalloc would break.
  * Its scratch (the packed v and q planes and the grid descriptor) lives in a
  * file-scope device array of 2^21 binary64 values per plane (about 32 MiB in
  * all), which every GPU that loads the library keeps until the process exits.
@@ -179,10 +181,12 @@ int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream);
  * that first call before any stream capture. All calls share the one array and
  * each call overwrites it (clearing it first): calls that overlap on the GPU --
  * from different streams or threads -- race and must not be issued. The call
- * synchronises cuda_stream before returning. Errors: PCG_EINVAL, PCG_ECUDA. */
+ * synchronises cuda_stream before returning. Errors: PCG_EINVAL, PCG_ECUDA,
+ * PCG_ETIMEOUT (a bounded device wait gave up; q is incomplete). */
 int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void *cuda_stream);
 
-/* s = Z D^-1 Z^T r on the device kernels of the iteration (the preconditioning step of Algorithm 1). */
+/* s = Z D^-1 Z^T r on the device kernels of the iteration (the preconditioning
+ * step of Algorithm 1). Same errors as pcg_spmv. */
 int pcg_precond_apply(pcg_handle *h, const double *r, double *s, void *cuda_stream);
 
 /* Export the library's own factor for comparison: for each wet point k in

@@ -236,13 +236,6 @@ static int upload_planes(pcg_handle *h, DevPlanes<T> &P, cudaStream_t s) {
   return PCG_OK;
 }
 
-static uint64_t default_timeout_ns() {
-  const char *e = getenv("PCG_WAIT_TIMEOUT_MS");
-  double ms = e ? atof(e) : 2000.0;
-  if (!(ms > 0)) ms = 2000.0;
-  return (uint64_t)(ms * 1e6);
-}
-
 static KParams kparams(const LoopPlan &L, const PlanGroup &g, int kind, int use_cond, int guard) {
   KParams p{};
   p.grids = g.gd_dev;
@@ -797,6 +790,22 @@ void mixed_stats(Member &m) {
   m.stats->true_relres = m.relres64;
 }
 
+int apply_status_clear(SolveState *st, cudaStream_t s) {
+  CK(cudaMemsetAsync(&st->status, 0, sizeof(int32_t), s));
+  return PCG_OK;
+}
+
+int apply_status_read(SolveState *st, cudaStream_t s) {
+  CK(cudaStreamSynchronize(s));
+  int32_t v = PCG_OK;
+  CK(cudaMemcpy(&v, &st->status, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (v != PCG_OK) {
+    set_error("a device wait of the apply gave up (" + status_name(v) + "); the output is incomplete");
+    return v;
+  }
+  return PCG_OK;
+}
+
 // Single-grid launches used by the server for the steps it runs per request.
 int single_launch(pcg_handle *h, bool f32, int which, int kind, cudaStream_t s) {
   LoopPlan &L = f32 ? *h->plan32 : *h->plan64;
@@ -1141,14 +1150,14 @@ int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream) {
   cudaStream_t s = (cudaStream_t)cuda_stream;
   auto &P = h->p64;
   int rc;
+  if ((rc = apply_status_clear(P.st, s))) return rc;
   if ((rc = pack_user(h, h->p64, v, 3, s))) return rc;
   KParams p{};
   p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K1_SPMV; p.dbg_skip_unit = -1;
   p.timeout_ns = default_timeout_ns();
   if ((rc = launch_k(P.ks, 1, P.n_units, p, s))) return rc;
   if ((rc = unpack_user(h, h->p64, q, 2, s))) return rc;
-  CK(cudaStreamSynchronize(s));
-  return PCG_OK;
+  return apply_status_read(P.st, s);
 }
 
 int pcg_precond_apply(pcg_handle *h, const double *r, double *sv, void *cuda_stream) {
@@ -1156,14 +1165,14 @@ int pcg_precond_apply(pcg_handle *h, const double *r, double *sv, void *cuda_str
   cudaStream_t s = (cudaStream_t)cuda_stream;
   auto &P = h->p64;
   int rc;
+  if ((rc = apply_status_clear(P.st, s))) return rc;
   if ((rc = pack_user(h, h->p64, r, 2, s))) return rc;
   KParams p{};
   p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = K2_APPLY; p.dbg_skip_unit = -1;
   p.timeout_ns = default_timeout_ns();
   if ((rc = launch_k(P.ks, 2, P.n_units, p, s))) return rc;
   if ((rc = unpack_user(h, h->p64, sv, 1, s))) return rc;
-  CK(cudaStreamSynchronize(s));
-  return PCG_OK;
+  return apply_status_read(P.st, s);
 }
 
 int pcg_apply_f32(pcg_handle *h, int32_t op, const double *v, double *out, void *cuda_stream) {
@@ -1173,6 +1182,7 @@ int pcg_apply_f32(pcg_handle *h, int32_t op, const double *v, double *out, void 
   if ((rc = ensure_f32(h, s))) return rc;
   auto &P = h->p32;
   // op 0: v into d[0], q = A v; op 1: v into r[0], s = M^-1 v
+  if ((rc = apply_status_clear(P.st, s))) return rc;
   if ((rc = pack_user(h, P, v, op == 0 ? 3 : 2, s))) return rc;
   KParams p{};
   p.grids = P.gd_dev; p.units = P.units_dev; p.ls = h->ls; p.kind = op == 0 ? (int)K1_SPMV : (int)K2_APPLY;
@@ -1180,8 +1190,7 @@ int pcg_apply_f32(pcg_handle *h, int32_t op, const double *v, double *out, void 
   p.timeout_ns = default_timeout_ns();
   if ((rc = launch_k(P.ks, op == 0 ? 1 : 2, P.n_units, p, s))) return rc;
   if ((rc = unpack_user(h, P, out, op == 0 ? 2 : 1, s))) return rc;
-  CK(cudaStreamSynchronize(s));
-  return PCG_OK;
+  return apply_status_read(P.st, s);
 }
 
 int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, int32_t prec, double *ms_stencil,

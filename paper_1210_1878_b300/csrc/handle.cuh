@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <memory>
 #include <string>
 #include <vector>
@@ -52,6 +53,15 @@ inline int wide_width(int elem_size, int pattern) {
 inline bool valid_width(int tx, int pattern) {
   return tx == 64 || tx == 128 || tx == exact_width(8, pattern) || tx == exact_width(4, pattern) ||
          tx == wide_width(8, pattern);
+}
+
+// Bound on every device wait of a launch (mbarrier waits of the streamed
+// rings): PCG_WAIT_TIMEOUT_MS milliseconds if set and positive, else 2 s.
+inline uint64_t default_timeout_ns() {
+  const char *e = getenv("PCG_WAIT_TIMEOUT_MS");
+  double ms = e ? atof(e) : 2000.0;
+  if (!(ms > 0)) ms = 2000.0;
+  return (uint64_t)(ms * 1e6);
 }
 
 // kernel sets per precision and strip width (kernels_*.cu)
@@ -184,6 +194,12 @@ void mixed_stats(Member &m);
 // which: 1 stencil kernel, 2 preconditioner kernel, 0 final x update; kind: K1_* / K2_*
 int single_launch(pcg_handle *h, bool f32, int which, int kind, cudaStream_t s);
 int plan_build(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls, cudaStream_t s);
+// One-operand applies (no solve state of their own): clear the status word of
+// the grid's device state before the launch; after it, synchronise the stream
+// and return the status a kernel recorded there (PCG_ETIMEOUT when one of its
+// bounded waits gave up), PCG_OK otherwise.
+int apply_status_clear(SolveState *st, cudaStream_t s);
+int apply_status_read(SolveState *st, cudaStream_t s);
 std::string status_name(int s);
 void fill_opts(const pcg_opts *o, pcg_opts &out);
 bool is_device_ptr(const void *p);

@@ -5,7 +5,9 @@
 // file-scope device array instead: the packed input plane, the packed output
 // plane and the grid descriptor the kernels read. It calls no cudaMalloc,
 // cudaFree or other allocating routine, so it can be used by callers that own
-// all device memory themselves or must not allocate at the point of the call.
+// all device memory themselves (an ocean model whose memory manager claims the
+// whole device at start-up) or that run under a fixed device-memory budget
+// where a hidden allocation at the point of the call would break it.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -82,6 +84,9 @@ extern "C" int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void 
   gd.d[0] = plane_v + origin;
   gd.d[1] = plane_v + origin;
   gd.q = plane_q + origin;
+  // the kernels record a bounded wait that gave up in the handle's state
+  int rc_st = apply_status_clear(P.st, s);
+  if (rc_st) return rc_st;
   CK(cudaMemcpyAsync(b8, &gd, sizeof(gd), cudaMemcpyHostToDevice, s));
   // the scratch keeps the previous call's contents: land strips, ghost rows and
   // columns must read zero
@@ -94,7 +99,7 @@ extern "C" int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void 
     p.ls = h->ls;
     p.kind = K1_SPMV;
     p.dbg_skip_unit = -1;
-    p.timeout_ns = 2000000000ull;
+    p.timeout_ns = default_timeout_ns();
     const double *vin = v;
     int which = 3;
     void *pack_args[] = {&p, (void *)&vin, &which};
@@ -110,6 +115,6 @@ extern "C" int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void 
   const size_t n = (size_t)P.nx * P.ny;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
   CK(cudaLaunchKernel(P.ks.unpack, dim3(blocks > 0 ? blocks : 1), dim3(256), un_args, 0, s));
-  CK(cudaStreamSynchronize(s));
-  return PCG_OK;
+  // synchronises s; PCG_ETIMEOUT if a wait of the stencil launch gave up
+  return apply_status_read(P.st, s);
 }

@@ -4,11 +4,13 @@ launches, the graph loop.
 
 Element by element against the oracle: q = A v (Section 3, Eq. 9) and
 s = Z D^-1 Z^T r (the preconditioning step of Algorithm 1) over every point,
-with the rounding bounds of the smaller parity tests. For whole solves, which
-the oracle would take about a minute to repeat here: the iteration count
-within 2 of the oracle's count for the same grid and right-hand side (recorded
-by ``oracle/record_iterations.py``), and the true relative residual of the
-returned x, recomputed by the oracle, at most 1e-10 (both precisions)."""
+with the rounding bounds of the smaller parity tests. For whole solves: the
+iteration count within 2 of the oracle's count for the same grid and
+right-hand side (recorded by ``oracle/record_iterations.py``), the true
+relative residual of the returned x, recomputed by the oracle, at most 1e-10,
+and x within 1e-8 of the tight reference solution (the oracle's own PCG run
+to 1e-13, about a minute of CPU time, computed once for all four solves),
+in both precisions."""
 import json
 import os
 
@@ -18,6 +20,7 @@ import scipy.sparse as sp
 
 import gridgen
 import oracle
+from oracle_checks import tight_reference
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +42,13 @@ def full():
     yield pcg, g, P, hs
     for h in hs.values():
         h.close()
+
+
+@pytest.fixture(scope="module")
+def x_ref(full):
+    """A x_ref = b for the benchmark's right-hand side, by the oracle alone."""
+    pcg, g, P, hs = full
+    return tight_reference(P, P.to_wet(g.b))
 
 
 def _csr(P):
@@ -82,7 +92,7 @@ def test_full_size_precond(full):
 @pytest.mark.parametrize("pattern,prec,key", [(1, 0, "orca12-fp64"), (0, 0, "orca12-fp64-trilA"),
                                               (1, 1, None), (0, 1, None)],
                          ids=["trilA2-fp64", "trilA-fp64", "trilA2-mixed", "trilA-mixed"])
-def test_full_size_solve(full, pattern, prec, key):
+def test_full_size_solve(full, x_ref, pattern, prec, key):
     pcg, g, P, hs = full
     b = torch.from_numpy(g.b).cuda()
     x = torch.zeros_like(b)
@@ -93,9 +103,12 @@ def test_full_size_solve(full, pattern, prec, key):
     xg = x.cpu().numpy()
     assert np.all(xg[g.wet == 0] == 0)
     bw = P.to_wet(g.b)
-    true_rel = np.linalg.norm(bw - P.spmv(P.to_wet(xg))) / np.linalg.norm(bw)
+    xw = P.to_wet(xg)
+    true_rel = np.linalg.norm(bw - P.spmv(xw)) / np.linalg.norm(bw)
     assert true_rel <= 1e-10 * (1 + 1e-3), true_rel
     assert abs(st.true_relres - true_rel) <= 1e-3 * 1e-10 + 1e-3 * true_rel
+    err = np.linalg.norm(xw - x_ref) / np.linalg.norm(x_ref)
+    assert err <= 1e-8, err
 
 
 def test_full_size_f32_kernels(full):
