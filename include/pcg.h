@@ -27,8 +27,10 @@
  *     pinned); host buffers are copied through the handle's staging buffer on
  *     the given stream. The caller owns every buffer it passes.
  *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
- *     stream). Calls that return results (solves, applies) synchronise that
- *     stream before returning.
+ *     stream). Solves (pcg_solve, pcg_solve_batched) are enqueued on that
+ *     stream and return at once; their x and statistics are valid after
+ *     pcg_sync. The one-operand applies synchronise the stream before
+ *     returning.
  *   - A handle owns all device memory it allocates; it is not thread-safe
  *     (one thread at a time). The solver server is thread-safe.
  */
@@ -143,23 +145,47 @@ typedef struct pcg_handle pcg_handle;
  * PCG_ENOMEM, PCG_ECUDA. */
 int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, pcg_handle **out);
 
-/* Solve A x = b (Algorithm 1). b: [ny][nx] binary64; x: [ny][nx] binary64,
- * read as the initial guess when opts->use_x0, always written with the
- * solution (land = 0). opts may be NULL (rtol 1e-10, FP64). Blocks until the
- * solve is finished; stats (may be NULL) are then valid.
- * Returns the solve status: PCG_OK, PCG_ENOTCONV (x holds the last iterate),
- * PCG_EBREAKDOWN, PCG_ETIMEOUT, PCG_EINVAL, PCG_ECUDA. */
+/* Solve A x = b (Algorithm 1 with its stopping rule): enqueue the whole solve
+ * on cuda_stream and return without waiting for it. b: [ny][nx] binary64; x:
+ * [ny][nx] binary64, read as the initial guess when opts->use_x0, written
+ * with the solution (land = 0). opts may be NULL (rtol 1e-10, FP64).
+ * The solve runs on the device from start to end: the PCG iterations, the
+ * true-residual check at exit and the restarts from the true residual
+ * (PCG_FP64), or the refinement steps (PCG_MIXED), are decided by device
+ * kernels inside one CUDA graph launch, with no host round trip. x and *stats
+ * (stats may be NULL; otherwise it must stay valid until then) are valid after
+ * pcg_sync(h), which returns the solve's status: PCG_OK, PCG_ENOTCONV (x holds
+ * the last iterate), PCG_EBREAKDOWN, PCG_ETIMEOUT. This call returns PCG_OK once
+ * the solve is enqueued, or an error found before (PCG_EINVAL, PCG_ENOMEM,
+ * PCG_ECUDA). b may be reused as soon as the call returns.
+ * One solve may be in flight per handle: a call on a handle whose previous
+ * solve has not been synchronised first waits for it (as pcg_sync does), and so
+ * do the other entry points that use the handle. Host buffers: b is staged
+ * at the call; a pageable host x makes the call wait for the solve (the copy
+ * into pageable memory completes synchronously), a pinned one does not.
+ * Without conditional CUDA graphs (or with PCG_LOOP_CHUNKED set) the solve is
+ * done by a host-driven loop before the call returns; pcg_sync then only
+ * reports it. */
 int pcg_solve(pcg_handle *h, const double *b, double *x, const pcg_opts *opts, pcg_stats *stats,
               void *cuda_stream);
 
-/* Solve nbatch independent systems, one per handle (handles may repeat only
- * with distinct b/x buffers), advancing all of them in lock-step: every
- * device launch covers the work of all unconverged members, and converged
- * members drop out. Each member's result equals what pcg_solve gives for it
- * alone (same kernels, same per-grid reduction order). stats: [nbatch].
- * Returns PCG_OK if every member converged, else the first failing status. */
+/* Solve nbatch independent systems, one per handle (each handle at most
+ * once), advancing all of them in lock-step: every device launch covers the
+ * work of all unconverged members, and converged members drop out. Each
+ * member's result equals what pcg_solve gives for it alone (same kernels, same
+ * per-grid reduction order). Enqueued like pcg_solve; stats ([nbatch], may be
+ * NULL) and every x are valid after pcg_sync on any member, which returns
+ * PCG_OK if every member converged, else the first failing member's status.
+ * The plans and graph of a batch are kept for later calls on the same handles
+ * (the four most recent batches). */
 int pcg_solve_batched(pcg_handle *const *hs, int32_t nbatch, const double *const *b, double *const *x,
                       const pcg_opts *opts, pcg_stats *stats, void *cuda_stream);
+
+/* Wait for the solve enqueued on h (pcg_solve or pcg_solve_batched), fill its
+ * statistics and return its status (see pcg_solve_batched for a batch). With
+ * nothing in flight, returns the status of h's last synchronised solve
+ * (PCG_OK if none). PCG_ECUDA if the stream reported an error. */
+int pcg_sync(pcg_handle *h);
 
 /* q = A v on the device kernels of the iteration (Section 3, Eq. 9).
  * Returns PCG_OK, PCG_EINVAL, PCG_ECUDA, or PCG_ETIMEOUT when a bounded device
@@ -253,6 +279,16 @@ int pcg_tiles(pcg_handle *h, int32_t prec, int32_t *tile_x, int32_t *tile_y);
  * PCG_ECUDA. */
 int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, int32_t prec, double *ms_stencil,
                         double *ms_precond, void *cuda_stream);
+
+/* Measurement entry point (no counterpart in the paper): the binary64
+ * fused multiply-add rate of the current GPU, the unit that bounds the binary64
+ * iteration on this part. Runs one warm-up and then `launches` launches of a
+ * kernel in which every thread of one full wave of resident blocks advances 8
+ * independent FMA chains, times them with CUDA events on cuda_stream and
+ * writes the rate in TFLOP/s (2 flops per FMA) to *tflops and the mean launch
+ * time to *ms_per_launch (may be NULL). Allocates and frees a small device
+ * buffer. Errors: PCG_EINVAL (tflops NULL or launches <= 0), PCG_ECUDA. */
+int pcg_fp64_fma_rate(int32_t launches, double *tflops, double *ms_per_launch, void *cuda_stream);
 
 /* Number of kernel launches this library has issued since it was loaded,
  * counting every kernel run inside a loop graph. */

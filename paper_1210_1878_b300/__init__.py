@@ -25,10 +25,11 @@ PCG_PAT_TRIL_A, PCG_PAT_TRIL_A2, PCG_PAT_FULL, PCG_PAT_BAND_T, PCG_PAT_DIAG = ra
 PCG_FP64, PCG_MIXED = 0, 1
 
 EXPORTED = [
-    "ainv_setup", "ainv_factor_host", "pcg_solve", "pcg_solve_batched", "pcg_spmv", "pcg_spmv_noalloc", "pcg_precond_apply",
+    "ainv_setup", "ainv_factor_host", "pcg_solve", "pcg_solve_batched", "pcg_sync", "pcg_spmv", "pcg_spmv_noalloc", "pcg_precond_apply",
     "pcg_apply_f32", "pcg_autotune", "pcg_tiles",
     "pcg_ainv_export", "pcg_resident_bytes", "pcg_n_wet", "pcg_free", "pcg_status_string",
-    "pcg_last_error_message", "pcg_debug_wait_timeout", "pcg_profile_kernels", "pcg_kernel_launches", "solver_server_create", "solver_server_register", "solver_server_submit",
+    "pcg_last_error_message", "pcg_debug_wait_timeout", "pcg_profile_kernels", "pcg_kernel_launches",
+    "pcg_fp64_fma_rate", "solver_server_create", "solver_server_register", "solver_server_submit",
     "solver_server_wait", "solver_server_cancel", "solver_server_stats", "solver_server_destroy",
 ]
 
@@ -87,6 +88,7 @@ def _load():
         "pcg_solve": (C.c_int, [vp, vp, vp, C.POINTER(pcg_opts), C.POINTER(pcg_stats), vp]),
         "pcg_solve_batched": (C.c_int, [C.POINTER(vp), i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(pcg_opts),
                                         C.POINTER(pcg_stats), vp]),
+        "pcg_sync": (C.c_int, [vp]),
         "pcg_spmv": (C.c_int, [vp, vp, vp, vp]),
         "pcg_spmv_noalloc": (C.c_int, [vp, vp, vp, vp]),
         "pcg_precond_apply": (C.c_int, [vp, vp, vp, vp]),
@@ -102,6 +104,7 @@ def _load():
         "pcg_debug_wait_timeout": (C.c_int, [vp, i32, dbl, vp]),
         "pcg_profile_kernels": (C.c_int, [vp, vp, i32, i32, C.POINTER(dbl), C.POINTER(dbl), vp]),
         "pcg_kernel_launches": (C.c_uint64, []),
+        "pcg_fp64_fma_rate": (C.c_int, [i32, C.POINTER(dbl), C.POINTER(dbl), vp]),
         "solver_server_create": (C.c_int, [C.POINTER(pcg_server_opts), C.POINTER(vp)]),
         "solver_server_register": (C.c_int, [vp, vp, C.POINTER(i32)]),
         "solver_server_submit": (C.c_int, [vp, i32, vp, vp, i32, DONE_CB, vp, C.POINTER(C.c_uint64)]),
@@ -170,6 +173,7 @@ class Handle:
     def __init__(self, ptr, nx, ny):
         self._p = C.c_void_p(ptr)
         self.nx, self.ny = nx, ny
+        self._inflight = None      # arguments of an enqueued solve, kept alive until pcg_sync
 
     @property
     def ptr(self):
@@ -231,17 +235,36 @@ def make_opts(rtol=1e-10, max_iter=0, prec=PCG_FP64, inner_rtol=0.0, max_outer=0
                     int(max_replace))
 
 
-def pcg_solve(h: Handle, b, x, opts: pcg_opts | None = None, stream=None, check=True) -> pcg_stats:
+def pcg_solve(h: Handle, b, x, opts: pcg_opts | None = None, stream=None, check=True, sync=True) -> pcg_stats:
+    """Enqueue one solve; with sync (default) wait for it (pcg_sync) and return
+    its statistics (.rc holds the status). With sync=False the statistics are
+    filled by a later ``pcg_sync(h)``; keep b, x and the returned object alive
+    until then."""
     st = pcg_stats()
     o = opts if opts is not None else make_opts()
     rc = lib.pcg_solve(h.ptr, _ptr(b), _ptr(x), C.byref(o), C.byref(st), _stream(stream))
-    if check and rc not in (PCG_OK,):
-        raise PCGError(rc, "pcg_solve")
+    if rc != PCG_OK:
+        if check:
+            raise PCGError(rc, "pcg_solve")
+        st.rc = rc
+        return st
+    h._inflight = (st, o, b, x)
+    if sync:
+        rc = pcg_sync(h)
+        if check and rc != PCG_OK:
+            raise PCGError(rc, "pcg_solve")
     st.rc = rc
     return st
 
 
-def pcg_solve_batched(hs, bs, xs, opts: pcg_opts | None = None, stream=None, check=True):
+def pcg_sync(h: Handle) -> int:
+    """Wait for the solve enqueued on h and return its status (pcg_sync)."""
+    rc = int(lib.pcg_sync(h.ptr))
+    h._inflight = None
+    return rc
+
+
+def pcg_solve_batched(hs, bs, xs, opts: pcg_opts | None = None, stream=None, check=True, sync=True):
     n = len(hs)
     H = (C.c_void_p * n)(*[h.ptr for h in hs])
     B = (C.c_void_p * n)(*[_ptr(b) for b in bs])
@@ -249,6 +272,13 @@ def pcg_solve_batched(hs, bs, xs, opts: pcg_opts | None = None, stream=None, che
     stats = (pcg_stats * n)()
     o = opts if opts is not None else make_opts()
     rc = lib.pcg_solve_batched(H, n, B, X, C.byref(o), stats, _stream(stream))
+    if rc == PCG_OK:
+        for h in hs:
+            h._inflight = (stats, o, bs, xs)
+        if sync:
+            rc = pcg_sync(hs[0])
+            for h in hs:
+                h._inflight = None
     if check and rc != PCG_OK:
         raise PCGError(rc, "pcg_solve_batched")
     return rc, list(stats)
@@ -319,6 +349,15 @@ def pcg_profile_kernels(h: Handle, b, iters=20, prec=PCG_FP64, stream=None):
     if rc != PCG_OK:
         raise PCGError(rc, "pcg_profile_kernels")
     return a.value, c.value
+
+
+def pcg_fp64_fma_rate(launches=10, stream=None):
+    """Measured binary64 FMA rate of the current GPU: (TFLOP/s, ms per launch)."""
+    t, ms = C.c_double(), C.c_double()
+    rc = lib.pcg_fp64_fma_rate(int(launches), C.byref(t), C.byref(ms), _stream(stream))
+    if rc != PCG_OK:
+        raise PCGError(rc, "pcg_fp64_fma_rate")
+    return t.value, ms.value
 
 
 def pcg_kernel_launches() -> int:

@@ -250,6 +250,7 @@ static KParams kparams(const LoopPlan &L, const PlanGroup &g, int kind, int use_
 }
 
 static std::atomic<uint64_t> g_launches{0};
+void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 static int launch(const void *f, int grid, int block, size_t smem, KParams p, cudaStream_t s) {
   if (grid <= 0) return PCG_OK;
@@ -514,10 +515,9 @@ void fill_opts(const pcg_opts *o, pcg_opts &out) {
 // Inputs of one member: b, x0 (or x = 0; with pack_x0 false and use_x0 set,
 // the x plane keeps the grid's last solution: a warm start), zeroed
 // directions, and the device state.
-int member_load(Member &m, const pcg_opts &o, bool pack_x0, cudaStream_t s) {
+static int member_inputs(Member &m, const pcg_opts &o, bool pack_x0, cudaStream_t s) {
   auto &P = m.h->p64;
   int rc;
-  const int max_iter = o.max_iter > 0 ? o.max_iter : std::max(m.h->G.n, 1);
   if ((rc = pack_user(m.h, m.h->p64, m.b, 0, s))) return rc;
   if (o.use_x0) {
     if (pack_x0 && (rc = pack_user(m.h, m.h->p64, m.x, 1, s))) return rc;
@@ -525,8 +525,19 @@ int member_load(Member &m, const pcg_opts &o, bool pack_x0, cudaStream_t s) {
     CK(cudaMemsetAsync(P.plane_start(P.vec(0)), 0, P.plane_elems * sizeof(double), s));
   }
   for (int v : {5, 6}) CK(cudaMemsetAsync(P.plane_start(P.vec(v)), 0, P.plane_elems * sizeof(double), s));
+  return PCG_OK;
+}
+
+int member_pack(Member &m, const pcg_opts &o, cudaStream_t s) { return member_inputs(m, o, true, s); }
+
+int member_load(Member &m, const pcg_opts &o, bool pack_x0, cudaStream_t s) {
+  auto &P = m.h->p64;
+  int rc;
+  const int max_iter = o.max_iter > 0 ? o.max_iter : std::max(m.h->G.n, 1);
+  if ((rc = member_inputs(m, o, pack_x0, s))) return rc;
   SolveState &st = *m.st_host;
   std::memset(&st, 0, sizeof(st));
+  st.final_status = -1;
   st.rtol = o.rtol;
   st.max_iter = max_iter;
   st.status = PCG_OK;
@@ -601,8 +612,8 @@ void member_stats(Member &m) {
 
 // Binary64 solve of every member of the plan: Algorithm 1 on the device, the
 // true-residual check, and restarts from the true residual where it fails.
-static int solve_members64(LoopPlan &L, LaunchState *ls_host, std::vector<Member> &M, const pcg_opts &o,
-                           cudaStream_t s) {
+int solve_members64(LoopPlan &L, LaunchState *ls_host, std::vector<Member> &M, const pcg_opts &o,
+                    cudaStream_t s) {
   int rc;
   int max_iter_all = 0;
   for (auto &m : M) {
@@ -661,6 +672,7 @@ bool mixed_prepare_inner(Member &m, const pcg_opts &o, int budget, int outer, cu
   }
   SolveState st32{};
   st32.status = PCG_OK;
+  st32.final_status = -1;
   if (fs >= 0) {
     m.final_status = fs;
     st.retired = 1; st.done = 1;
@@ -681,9 +693,6 @@ bool mixed_prepare_inner(Member &m, const pcg_opts &o, int budget, int outer, cu
       g_launches.fetch_add(1, std::memory_order_relaxed);
       if (cudaLaunchKernel(f, dim3(m.h->p64.n_units), dim3(m.h->tx), args, 0, s) != cudaSuccess) *err = PCG_ECUDA;
     }
-    if (cudaMemsetAsync(P32.plane_start(P32.vec(0)), 0, P32.plane_elems * sizeof(float), s) != cudaSuccess) *err = PCG_ECUDA;
-    for (int v : {5, 6})
-      if (cudaMemsetAsync(P32.plane_start(P32.vec(v)), 0, P32.plane_elems * sizeof(float), s) != cudaSuccess) *err = PCG_ECUDA;
     // Inner tolerance. Far from the finish: o.inner_rtol (the binary32 solve
     // cannot go much below ~1e-6 relative). Within a decade of the finish
     // (the reduction still needed, rtol / relres, is at least inner_rtol / 10):
@@ -750,6 +759,7 @@ int solve_members_mixed(LoopPlan &L64, LoopPlan &L32, LaunchState *ls_host, std:
       if (m.final_status >= 0) {
         SolveState st32{};
         st32.status = PCG_OK; st32.done = 1; st32.retired = 1;
+        st32.final_status = -1;
         *m.h->st32_host = st32;
         CK(cudaMemcpyAsync(m.h->p32.st, m.h->st32_host, sizeof(SolveState), cudaMemcpyHostToDevice, s));
         continue;
@@ -933,6 +943,7 @@ static int retile(pcg_handle *h, int prec, int tx, int ty, cudaStream_t s) {
   int rc;
   if (prec == PCG_MIXED) {
     if (h->plan32 && h->tx32 == tx && h->ty32 == ty) return PCG_OK;
+    h->version++;                                   // cached batch plans of the old planes no longer match
     if (h->plan32) h->bytes -= h->p32.bytes;
     h->plan32.reset();
     h->p32.release();
@@ -943,7 +954,9 @@ static int retile(pcg_handle *h, int prec, int tx, int ty, cudaStream_t s) {
   }
   if (h->tx == tx && h->ty == ty) return PCG_OK;
   CK(cudaStreamSynchronize(s));
+  h->version++;
   h->bytes -= h->p64.bytes;
+  if (h->plan32) { h->plan32->solve.reset(); h->plan32->solve_tried = false; }   // it spans the binary64 planes too
   h->plan64.reset();
   h->p64.release();
   h->p64 = DevPlanes<double>{};
@@ -1035,6 +1048,7 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
   *out = nullptr;
   try {
     auto h = std::make_unique<pcg_handle>();
+    handle_init_serial(h.get());
     int rc = factor_host(grid, opts, h->G, h->F);
     if (rc) return rc;
     h->pattern = opts->pattern;
@@ -1086,67 +1100,9 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
   }
 }
 
-int pcg_solve(pcg_handle *h, const double *b, double *x, const pcg_opts *opts, pcg_stats *stats, void *cuda_stream) {
-  pcg_handle *hs[1] = {h};
-  const double *bs[1] = {b};
-  double *xs[1] = {x};
-  return pcg_solve_batched(hs, 1, bs, xs, opts, stats, cuda_stream);
-}
-
-int pcg_solve_batched(pcg_handle *const *hs, int32_t nbatch, const double *const *b, double *const *x,
-                      const pcg_opts *opts, pcg_stats *stats, void *cuda_stream) {
-  const auto t0 = std::chrono::steady_clock::now();
-  if (!hs || nbatch <= 0 || !b || !x) { set_error("invalid batch arguments"); return PCG_EINVAL; }
-  for (int i = 0; i < nbatch; ++i) {
-    if (!hs[i] || !b[i] || !x[i]) { set_error("NULL handle or vector in batch"); return PCG_EINVAL; }
-    for (int k = 0; k < i; ++k)
-      if (hs[k] == hs[i]) { set_error("a handle may appear once per batch"); return PCG_EINVAL; }
-  }
-  pcg_opts o;
-  fill_opts(opts, o);
-  if (o.prec != PCG_FP64 && o.prec != PCG_MIXED) { set_error("unknown precision"); return PCG_EINVAL; }
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  std::vector<Member> M(nbatch);
-  for (int i = 0; i < nbatch; ++i) {
-    M[i].h = hs[i]; M[i].b = b[i]; M[i].x = x[i]; M[i].stats = stats ? &stats[i] : nullptr;
-    M[i].st_host = hs[i]->st_host;
-  }
-  int rc;
-  if (o.prec == PCG_MIXED) {
-    for (int i = 0; i < nbatch; ++i)
-      if ((rc = ensure_f32(hs[i], s))) return rc;
-    if (nbatch == 1) {
-      if ((rc = plan_single(hs[0]))) return rc;
-      rc = solve_members_mixed(*hs[0]->plan64, *hs[0]->plan32, hs[0]->ls_host, M, o, s);
-    } else {
-      LoopPlan L64, L32;
-      if ((rc = plan_build(L64, hs, nbatch, false, hs[0]->ls, s))) return rc;
-      if ((rc = plan_build32(L32, hs, nbatch, true, hs[0]->ls, s))) return rc;
-      rc = solve_members_mixed(L64, L32, hs[0]->ls_host, M, o, s);
-      cudaStreamSynchronize(s);
-    }
-  } else if (nbatch == 1) {
-    if ((rc = plan_single(hs[0]))) return rc;
-    rc = solve_members64(*hs[0]->plan64, hs[0]->ls_host, M, o, s);
-  } else {
-    LoopPlan L;
-    if ((rc = plan_build(L, hs, nbatch, true, hs[0]->ls, s))) return rc;
-    rc = solve_members64(L, hs[0]->ls_host, M, o, s);
-    cudaStreamSynchronize(s);
-  }
-  if (rc) return rc;
-  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  int first_bad = PCG_OK;
-  for (int i = 0; i < nbatch; ++i) {
-    if (stats) stats[i].seconds = secs;
-    if (M[i].final_status != PCG_OK && first_bad == PCG_OK) first_bad = M[i].final_status;
-  }
-  if (first_bad != PCG_OK) set_error("solve finished with status: " + status_name(first_bad));
-  return first_bad;
-}
-
 int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream) {
   if (!h || !v || !q) { set_error("NULL argument"); return PCG_EINVAL; }
+  handle_finish_pending(h);   // one piece of work in flight per handle
   cudaStream_t s = (cudaStream_t)cuda_stream;
   auto &P = h->p64;
   int rc;
@@ -1162,6 +1118,7 @@ int pcg_spmv(pcg_handle *h, const double *v, double *q, void *cuda_stream) {
 
 int pcg_precond_apply(pcg_handle *h, const double *r, double *sv, void *cuda_stream) {
   if (!h || !r || !sv) { set_error("NULL argument"); return PCG_EINVAL; }
+  handle_finish_pending(h);   // one piece of work in flight per handle
   cudaStream_t s = (cudaStream_t)cuda_stream;
   auto &P = h->p64;
   int rc;
@@ -1177,6 +1134,7 @@ int pcg_precond_apply(pcg_handle *h, const double *r, double *sv, void *cuda_str
 
 int pcg_apply_f32(pcg_handle *h, int32_t op, const double *v, double *out, void *cuda_stream) {
   if (!h || !v || !out || (op != 0 && op != 1)) { set_error("invalid arguments"); return PCG_EINVAL; }
+  handle_finish_pending(h);   // one piece of work in flight per handle
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int rc;
   if ((rc = ensure_f32(h, s))) return rc;
@@ -1196,6 +1154,7 @@ int pcg_apply_f32(pcg_handle *h, int32_t op, const double *v, double *out, void 
 int pcg_profile_kernels(pcg_handle *h, const double *b, int32_t iters, int32_t prec, double *ms_stencil,
                         double *ms_precond, void *cuda_stream) {
   if (!h || !b || iters <= 0 || (prec != PCG_FP64 && prec != PCG_MIXED)) { set_error("invalid arguments"); return PCG_EINVAL; }
+  handle_finish_pending(h);   // one piece of work in flight per handle
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int rc;
   if ((rc = plan_single(h))) return rc;
@@ -1287,6 +1246,7 @@ int pcg_autotune(pcg_handle *h, int32_t prec, int32_t objective, int32_t *tile_x
     set_error("invalid arguments");
     return PCG_EINVAL;
   }
+  handle_finish_pending(h);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int rc, tx = 0, ty = 0;
   const int nx = h->G.nx, ny = h->G.ny;
@@ -1342,6 +1302,7 @@ int pcg_tiles(pcg_handle *h, int32_t prec, int32_t *tile_x, int32_t *tile_y) {
 
 void pcg_free(pcg_handle *h) {
   if (!h) return;
+  handle_finish_pending(h);
   h->plan64.reset();
   h->plan32.reset();
   h->p64.release();
@@ -1360,6 +1321,7 @@ void pcg_free(pcg_handle *h) {
 // the function reports the status the device recorded.
 int pcg_debug_wait_timeout(pcg_handle *h, int32_t unit, double timeout_ms, void *cuda_stream) {
   if (!h || unit < 0 || unit >= h->p64.n_units) { set_error("invalid arguments"); return PCG_EINVAL; }
+  handle_finish_pending(h);
   cudaStream_t s = (cudaStream_t)cuda_stream;
   auto &P = h->p64;
   SolveState st{};

@@ -46,8 +46,19 @@ struct SolveState {
   double rr, bb, dq, rr_true;         // last reductions
   double rtol;
   int32_t iter, max_iter, status, done;
-  int32_t dsel, rsel, bzero, retired;   // retired: set by the host once the result is final
+  int32_t dsel, rsel, bzero, retired;   // retired: set once the result is final
   uint32_t cnt1, cnt2, pad2, pad3;    // arrival counters of the two kernels
+  // Control of a whole solve, decided on the device between passes (the
+  // true-residual restarts of a binary64 solve; the refinement steps of a
+  // mixed-precision solve, kept in the binary64 state).
+  int32_t final_status;               // pcg_status once the result is final, else -1
+  int32_t pad4;
+  int32_t replacements, max_replace;  // restarts taken / allowed
+  double scale;                       // mixed: power of two scaling the residual into binary32
+  double relres64;                    // mixed: binary64 ||b - A x|| / ||b|| of the last refinement step
+  double inner_rtol;                  // mixed: tolerance of an inner solve far from the finish
+  int32_t inner_iters, inner_solves;  // mixed: inner iterations and inner solves so far
+  int32_t budget, max_outer;          // mixed: cap on inner iterations in total, on refinement steps
 };
 
 struct LaunchState {
@@ -60,6 +71,8 @@ struct LaunchState {
   uint64_t budget_ns;      // wall-clock cap on the loop (a runaway guard)
   int32_t timed_out;
   int32_t cond_cleared;    // the loop condition has been cleared in this launch
+  int32_t bodies_total;    // loop-body executions over every pass of a solve (launch count)
+  int32_t passes;          // outer passes of a solve (restarts / refinement steps + 1)
 };
 
 // A CUtensorMap as the kernels see it: 128 opaque bytes, 64-byte aligned.

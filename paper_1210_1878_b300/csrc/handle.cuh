@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cstdlib>
 #include <memory>
 #include <string>
@@ -111,6 +112,23 @@ struct DevPlanes {
   }
 };
 
+// A whole-solve graph (csrc/solve.cu) over the members of a plan: outer
+// conditional loop of passes, inner conditional loop of PCG iterations.
+struct SolveGraph {
+  cudaGraphExec_t exec = nullptr;
+  SolveState **st64 = nullptr, **st32 = nullptr;   // device arrays of the members' states
+  int32_t *n_wet = nullptr;                         // device array of the members' wet counts
+  int n = 0;
+  int outer_kernels = 0;    // kernel nodes of one pass outside the inner loop
+  int inner_kernels = 0;    // kernel nodes of one inner loop body
+  ~SolveGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaFree(st64);
+    cudaFree(st32);
+    cudaFree(n_wet);
+  }
+};
+
 // The grids advanced together by one loop: grouped by kernel set, each group
 // with its descriptor array and concatenated unit list on the device.
 struct PlanGroup {
@@ -128,11 +146,16 @@ struct LoopPlan {
   bool graph_ok = false;
   int body_kernels = 0;            // kernel nodes in the loop body
   std::vector<void *> owned;       // device allocations of a batch plan
+  std::unique_ptr<SolveGraph> solve;   // whole-solve graph of a handle alone (built on first use)
+  bool solve_tried = false;            // its construction was attempted (and may have failed)
   ~LoopPlan() {
+    solve.reset();
     if (exec) cudaGraphExecDestroy(exec);
     for (void *p : owned) cudaFree(p);
   }
 };
+
+struct Pending;
 
 }  // namespace pcg
 
@@ -153,7 +176,30 @@ struct pcg_handle {
   std::unique_ptr<pcg::LoopPlan> plan64;
   std::unique_ptr<pcg::LoopPlan> plan32;
   size_t bytes = 0;
+  uint64_t serial = 0;                    // process-unique number of this handle
+  uint32_t version = 0;                   // bumped whenever its device planes are rebuilt
+  std::shared_ptr<pcg::Pending> pending;  // the solve enqueued on it and not yet synchronised
+  int last_status = PCG_OK;               // status of its last synchronised solve
 };
+
+namespace pcg {
+
+// A solve call enqueued and not yet synchronised (pcg_sync). Every member
+// handle of the call points to it.
+struct Pending {
+  std::shared_ptr<void> keep;             // batch plan whose graph the enqueued work runs
+  std::vector<pcg_handle *> hs;           // members, in call order
+  pcg_stats *stats = nullptr;             // caller's [hs.size()] statistics, filled at synchronisation
+  cudaStream_t s = nullptr;
+  bool mixed = false;
+  bool graph = false;                     // run by a whole-solve graph (else solved at the call)
+  int status = PCG_OK;                    // status of a call solved at the call
+  int outer_kernels = 0, inner_kernels = 0;
+  LaunchState *ls_host = nullptr;         // pinned copy of the launch state, for the launch count
+  std::chrono::steady_clock::time_point t0;
+};
+
+}  // namespace pcg
 
 namespace pcg {
 
@@ -174,6 +220,11 @@ struct Member {
 
 // phases of a solve, shared by pcg_solve_batched and the solver server
 int member_load(Member &m, const pcg_opts &o, bool pack_x0, cudaStream_t s);     // inputs and state
+int member_pack(Member &m, const pcg_opts &o, cudaStream_t s);                   // inputs only (b, x0, d = 0)
+int solve_members64(LoopPlan &L, LaunchState *ls_host, std::vector<Member> &M, const pcg_opts &o, cudaStream_t s);
+void handle_init_serial(pcg_handle *h);
+// Wait for the solve enqueued on h, if any, and release it; returns its status.
+int handle_finish_pending(pcg_handle *h);
 int members_arm(LoopPlan &L, LaunchState *ls_host, int active, int max_launches, cudaStream_t s);
 int members_init(LoopPlan &L, cudaStream_t s);                                   // r0, s0, rho0 for not-done grids
 int members_loop(LoopPlan &L, LaunchState *ls_host, int max_launches, cudaStream_t s);
@@ -199,6 +250,8 @@ int plan_build(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, Launc
 // and return the status a kernel recorded there (PCG_ETIMEOUT when one of its
 // bounded waits gave up), PCG_OK otherwise.
 int apply_status_clear(SolveState *st, cudaStream_t s);
+// Count kernel launches issued outside api.cu (pcg_kernel_launches).
+void note_launches(uint64_t n);
 int apply_status_read(SolveState *st, cudaStream_t s);
 std::string status_name(int s);
 void fill_opts(const pcg_opts *o, pcg_opts &out);

@@ -252,6 +252,7 @@ __device__ __forceinline__ void grid_finished(SolveState *st, LaunchState *ls, i
 // bodies, or when the wall-clock budget is spent.
 __device__ __forceinline__ void loop_guard(LaunchState *ls, const KParams &p) {
   const int l = atomicAdd(&ls->launches, 1) + 1;
+  ls->bodies_total += 1;
   const uint64_t now = global_ns();
   if (ls->t0_ns == 0) ls->t0_ns = now;
   const bool late = now - ls->t0_ns > ls->budget_ns;
@@ -1236,7 +1237,9 @@ __global__ void __launch_bounds__(TX) k_pack(KParams p, const U *user, int which
 
 // Mixed precision, refinement step: the binary64 residual r (plane r[rsel] of
 // the binary64 grid) scaled by a power of two becomes the binary32 right-hand
-// side b of the inner solve.
+// side b of the inner solve, whose solution x and directions d start at zero
+// (cleared here at the same points). scale 0: the scale the refinement step
+// chose on the device (SolveState::scale of the binary64 grid).
 // (one block of strip-width threads per unit of the binary64 planes)
 static __global__ void k_residual_to_f32(const GridDev<double> *g64, const GridDev<float> *g32, const Unit *units,
                                   double scale) {
@@ -1248,15 +1251,21 @@ static __global__ void k_residual_to_f32(const GridDev<double> *g64, const GridD
   const int col = un.sx * TX + threadIdx.x;
   const int j0 = un.sy * a.ty, rend = min(j0 + a.ty, a.ny);
   const double *r = a.r[a.st->rsel];
-  const double sc = scale;
+  const double sc = scale != 0.0 ? scale : a.st->scale;
   float *b = const_cast<float *>(f.b);
   if (col < a.nx)
-    for (int j = j0; j < rend; ++j)
-      store_dup(b + (size_t)j * f.pitch, col, a.nx, (float)(r[(size_t)j * a.pitch + col] * sc));
+    for (int j = j0; j < rend; ++j) {
+      const size_t ro = (size_t)j * f.pitch;
+      store_dup(b + ro, col, a.nx, (float)(r[(size_t)j * a.pitch + col] * sc));
+      store_dup(f.x + ro, col, a.nx, 0.0f);
+      store_dup(f.d[0] + ro, col, a.nx, 0.0f);
+      store_dup(f.d[1] + ro, col, a.nx, 0.0f);
+    }
 }
 
 // Mixed precision, refinement step: x += e / scale with e the binary32 inner
 // solution (x plane of the binary32 grid); the update is done in binary64.
+// inv_scale 0: 1 / SolveState::scale of the binary64 grid.
 // (one block of strip-width threads per unit of the binary64 planes)
 static __global__ void k_correct_f64(const GridDev<double> *g64, const GridDev<float> *g32, const Unit *units,
                               double inv_scale) {
@@ -1264,13 +1273,14 @@ static __global__ void k_correct_f64(const GridDev<double> *g64, const GridDev<f
   const Unit un = units[blockIdx.x];
   const GridDev<double> &a = g64[un.g];
   const GridDev<float> &f = g32[un.g];
-  if (*(volatile int32_t *)&a.st->retired) return;
+  if (*(volatile int32_t *)&a.st->retired || *(volatile int32_t *)&f.st->retired) return;
   const int col = un.sx * TX + threadIdx.x;
   const int j0 = un.sy * a.ty, rend = min(j0 + a.ty, a.ny);
+  const double inv = inv_scale != 0.0 ? inv_scale : 1.0 / a.st->scale;
   if (col < a.nx)
     for (int j = j0; j < rend; ++j) {
       double *xr = a.x + (size_t)j * a.pitch;
-      store_dup(xr, col, a.nx, fma(to_f64(f.x[(size_t)j * f.pitch + col]), inv_scale, xr[col]));
+      store_dup(xr, col, a.nx, fma(to_f64(f.x[(size_t)j * f.pitch + col]), inv, xr[col]));
     }
 }
 
@@ -1279,11 +1289,13 @@ template <typename T, typename U>
 __global__ void k_unpack(const GridDev<T> *gdp, U *user, int which) {
   const GridDev<T> &gd = *gdp;
   const T *srcp = which == 0 ? gd.x : which == 1 ? gd.s : which == 2 ? gd.q : gd.r[0];
+  // the solution of b = 0 is x = 0 whatever the x plane holds
+  const bool zero = which == 0 && gd.st->bzero != 0;
   const size_t n = (size_t)gd.nx * gd.ny;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     const int j = (int)(e / gd.nx), i = (int)(e % gd.nx);
     const size_t o = (size_t)j * gd.pitch + i;
-    user[e] = gd.a[o] > (T)0 ? (U)srcp[o] : (U)0;
+    user[e] = (gd.a[o] > (T)0 && !zero) ? (U)srcp[o] : (U)0;
   }
 }
 

@@ -60,6 +60,7 @@ int scratch_address(void **out) {
 extern "C" int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void *cuda_stream) {
   if (!h || !v || !q) { set_error("NULL argument"); return PCG_EINVAL; }
   if (!is_device_ptr(v) || !is_device_ptr(q)) { set_error("v and q must be device pointers"); return PCG_EINVAL; }
+  handle_finish_pending(h);   // one piece of work in flight per handle
   const DevPlanes<double> &P = h->p64;
   if (P.plane_elems > kMaxPlaneElems) {
     set_error("grid too large for the allocation-free scratch: padded plane of " + std::to_string(P.plane_elems) +
@@ -104,9 +105,11 @@ extern "C" int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void 
     int which = 3;
     void *pack_args[] = {&p, (void *)&vin, &which};
     CK(cudaLaunchKernel(P.ks.pack, dim3(P.n_units), dim3(P.tx), pack_args, 0, s));
+    note_launches(1);
     void *k_args[] = {&p};
     p.n_units = P.n_units;
     CK(cudaLaunchKernel(P.ks.k1[K1_SPMV], dim3(persistent_grid(P.ks, 1, P.n_units)), dim3(P.ks.tb), k_args, P.ks.smem1, s));
+    note_launches(1);
   }
   const GridDev<double> *gdp = reinterpret_cast<const GridDev<double> *>(b8);
   double *qout = q;
@@ -115,6 +118,7 @@ extern "C" int pcg_spmv_noalloc(pcg_handle *h, const double *v, double *q, void 
   const size_t n = (size_t)P.nx * P.ny;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
   CK(cudaLaunchKernel(P.ks.unpack, dim3(blocks > 0 ? blocks : 1), dim3(256), un_args, 0, s));
+  note_launches(1);
   // synchronises s; PCG_ETIMEOUT if a wait of the stencil launch gave up
   return apply_status_read(P.st, s);
 }

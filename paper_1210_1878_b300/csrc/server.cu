@@ -355,6 +355,7 @@ int solver_server_create(const pcg_server_opts *opts, pcg_server **out) {
 
 int solver_server_register(pcg_server *s, pcg_handle *h, int32_t *grid_id) {
   if (!s || !h || !grid_id) { set_error("NULL argument"); return PCG_EINVAL; }
+  handle_finish_pending(h);   // a solve enqueued on the handle before it joins the server
   std::lock_guard<std::mutex> lk(s->mu);
   for (auto &g : s->grids)
     if (g.h == h) { set_error("grid already registered"); return PCG_EINVAL; }

@@ -180,9 +180,15 @@ def test_true_residual_restart_path():
     assert ref.status == oracle.ENOTCONV and ref.replacements == 3
     st = pcg.pcg_solve(h, _dev(g.b), x, pcg.make_opts(rtol=5e-16, max_iter=5000, max_replace=3), check=False)
     assert st.status == pcg.PCG_ENOTCONV and st.replacements == 3 and st.outer_iters == 4, st.as_dict()
-    rel = float(np.linalg.norm(b - P.spmv(P.to_wet(x.cpu().numpy()))) / np.linalg.norm(b))
+    xw = P.to_wet(x.cpu().numpy())
+    rel = float(np.linalg.norm(b - P.spmv(xw)) / np.linalg.norm(b))
     assert rel <= 4 * ref.true_relres and rel <= 3e-15, (rel, ref.true_relres)
-    assert abs(st.true_relres - rel) <= 0.05 * rel
+    # at this level both residuals are rounding: each entry of b - A x carries
+    # at most gamma_6 (|b| + |A||x|) of binary64 error, on either side
+    rp, col, val, _, _ = P.csr()
+    A_abs = sp.csr_matrix((np.abs(val), col, rp), shape=(P.n, P.n))
+    floor = 2 * 6 * 2.0 ** -53 * np.linalg.norm(np.abs(b) + A_abs @ np.abs(xw)) / np.linalg.norm(b)
+    assert abs(st.true_relres - rel) <= floor, (st.true_relres, rel, floor)
     restarted = 0
     for rtol in (5e-15, 3e-15, 2e-15, 1e-15):
         ref = P.pcg(b, rtol=rtol, max_iter=5000, max_replace=3)
@@ -267,3 +273,42 @@ def test_strip_counts_beyond_16_bits_are_refused():
     assert st.status == pcg.PCG_OK
     bw = P.to_wet(g.b)
     assert np.linalg.norm(bw - P.spmv(P.to_wet(x.cpu().numpy()))) / np.linalg.norm(bw) <= 1e-10 * (1 + 1e-3)
+
+
+def test_async_solves_on_two_streams():
+    """The solve entry points enqueue the whole solve and return: two solves on
+    two streams (one binary64 restart-checked solve, one mixed-precision solve)
+    are issued back to back with no synchronisation in between, then pcg_sync
+    makes each result and its statistics valid; both meet the oracle's
+    acceptance. The first call returns while its solve is still running on the
+    device (the stopping test, the true-residual check and any restart are
+    decided there)."""
+    pcg = _pcg()
+    g1 = gridgen.make_grid(seed=gridgen.seed_for(2), **gridgen.ORCA025)
+    g2 = gridgen.make_grid(seed=gridgen.seed_for(1), **gridgen.COARSE)
+    h1 = pcg.ainv_setup_grid(g1, pattern=pcg.PCG_PAT_TRIL_A2, drop_tol=0.05)
+    h2 = pcg.ainv_setup_grid(g2, pattern=pcg.PCG_PAT_TRIL_A)
+    o1 = pcg.make_opts(rtol=1e-10)
+    o2 = pcg.make_opts(rtol=1e-10, prec=pcg.PCG_MIXED)
+    b1, b2 = _dev(g1.b), _dev(g2.b)
+    x1 = torch.zeros_like(b1)
+    x2 = torch.zeros_like(b2)
+    # first use builds the plans and graphs; the timed behaviour is the second
+    pcg.pcg_solve(h1, b1, x1, o1)
+    pcg.pcg_solve(h2, b2, x2, o2)
+    x1.zero_()
+    x2.zero_()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    st1 = pcg.pcg_solve(h1, b1, x1, o1, stream=s1, sync=False)
+    running = not s1.query()
+    st2 = pcg.pcg_solve(h2, b2, x2, o2, stream=s2, sync=False)
+    assert st1.rc == pcg.PCG_OK and st2.rc == pcg.PCG_OK
+    assert running, "pcg_solve waited for its solve"
+    assert pcg.pcg_sync(h2) == pcg.PCG_OK
+    assert pcg.pcg_sync(h1) == pcg.PCG_OK
+    assert pcg.pcg_sync(h1) == pcg.PCG_OK          # nothing in flight: the last status again
+    assert st1.status == pcg.PCG_OK and st1.iters > 0 and st2.status == pcg.PCG_OK and st2.outer_iters >= 1
+    for g, x, st in ((g1, x1, st1), (g2, x2, st2)):
+        P = oracle.OracleProblem.from_grid(g)
+        judge(P, g, P.to_wet(g.b), x.cpu().numpy(), rtol=1e-10, stats=st)
