@@ -180,14 +180,19 @@ def test_true_residual_restart_path():
     assert ref.status == oracle.ENOTCONV and ref.replacements == 3
     st = pcg.pcg_solve(h, _dev(g.b), x, pcg.make_opts(rtol=5e-16, max_iter=5000, max_replace=3), check=False)
     assert st.status == pcg.PCG_ENOTCONV and st.replacements == 3 and st.outer_iters == 4, st.as_dict()
-    xw = P.to_wet(x.cpu().numpy())
-    rel = float(np.linalg.norm(b - P.spmv(xw)) / np.linalg.norm(b))
-    assert rel <= 4 * ref.true_relres and rel <= 3e-15, (rel, ref.true_relres)
-    # at this level both residuals are rounding: each entry of b - A x carries
-    # at most gamma_6 (|b| + |A||x|) of binary64 error, on either side
     rp, col, val, _, _ = P.csr()
     A_abs = sp.csr_matrix((np.abs(val), col, rp), shape=(P.n, P.n))
-    floor = 2 * 6 * 2.0 ** -53 * np.linalg.norm(np.abs(b) + A_abs @ np.abs(xw)) / np.linalg.norm(b)
+
+    def residual_and_floor():
+        # at this level both sides' residuals are rounding: each entry of
+        # b - A x carries at most gamma_6 (|b| + |A||x|) of binary64 error
+        xw = P.to_wet(x.cpu().numpy())
+        rel = float(np.linalg.norm(b - P.spmv(xw)) / np.linalg.norm(b))
+        floor = 2 * 6 * 2.0 ** -53 * np.linalg.norm(np.abs(b) + A_abs @ np.abs(xw)) / np.linalg.norm(b)
+        return rel, floor
+
+    rel, floor = residual_and_floor()
+    assert rel <= 4 * ref.true_relres and rel <= 3e-15, (rel, ref.true_relres)
     assert abs(st.true_relres - rel) <= floor, (st.true_relres, rel, floor)
     restarted = 0
     for rtol in (5e-15, 3e-15, 2e-15, 1e-15):
@@ -196,8 +201,9 @@ def test_true_residual_restart_path():
             continue
         st = pcg.pcg_solve(h, _dev(g.b), x, pcg.make_opts(rtol=rtol, max_iter=5000, max_replace=3), check=False)
         assert st.status == pcg.PCG_OK, (rtol, st.as_dict())
-        rel = float(np.linalg.norm(b - P.spmv(P.to_wet(x.cpu().numpy()))) / np.linalg.norm(b))
-        assert rel <= rtol * (1 + 1e-3), (rtol, rel)
+        rel, floor = residual_and_floor()
+        # the device accepted on its own true residual, within rounding of the oracle's
+        assert st.true_relres <= rtol and rel <= rtol + floor, (rtol, st.true_relres, rel, floor)
         assert abs(st.replacements - ref.replacements) <= 1, (rtol, st.replacements, ref.replacements)
         restarted += st.replacements >= 1
     assert restarted >= 1
