@@ -14,7 +14,6 @@
 #include <memory>
 #include <map>
 #include <mutex>
-#include <queue>
 #include <tuple>
 #include <string>
 #include <vector>
@@ -143,61 +142,6 @@ static int upload_tensor_maps(DevPlanes<T> &P) {
   return PCG_OK;
 }
 
-// Rows of strip sx that hold a wet cell: row_wet[sx * ny + j].
-static std::vector<uint8_t> strip_rows(const HostGrid &G, int tx) {
-  const int ntx = (G.nx + tx - 1) / tx;
-  std::vector<uint8_t> row_wet((size_t)ntx * G.ny, 0);
-  for (int j = 0; j < G.ny; ++j)
-    for (int i = 0; i < G.nx; ++i)
-      if (G.idx[(size_t)j * G.nx + i] >= 0) row_wet[(size_t)(i / tx) * G.ny + j] = 1;
-  return row_wet;
-}
-
-// The unit list of a grid cut into strips tx columns wide: rectangles of a
-// strip holding a wet cell, of ty rows. When the grid has more such units
-// than `slots` (the resident CTAs that claim them), the top rows of every
-// strip are cut finer -- about `slots` units of ty/2 rows, then about `slots`
-// of ty/4 rows (at least 8 rows each) -- and listed after all the full-height
-// units: CTAs claim units in list order, so a launch ends on short units
-// instead of waiting for the CTAs that drew one full-height unit more. A
-// unit's index in the list is its slot in the reduction order.
-static std::vector<Unit> make_units(const HostGrid &G, int tx, int ty, int slots, const std::vector<uint8_t> &row_wet) {
-  const int ntx = (G.nx + tx - 1) / tx, ny = G.ny;
-  auto wet_in = [&](int sx, int j0, int j1) {
-    for (int j = j0; j < j1; ++j)
-      if (row_wet[(size_t)sx * ny + j]) return true;
-    return false;
-  };
-  int strips = 0;
-  long full_units = 0;
-  for (int sx = 0; sx < ntx; ++sx) {
-    if (wet_in(sx, 0, ny)) ++strips;
-    for (int j = 0; j < ny; j += ty) full_units += wet_in(sx, j, std::min(ny, j + ty)) ? 1 : 0;
-  }
-  int c1 = ny, c2 = ny;                              // tier boundaries (rows)
-  const int h1 = std::max(8, ty / 2 / 4 * 4), h2 = std::max(8, ty / 4 / 4 * 4);
-  if (strips > 0 && full_units > slots && h2 < ty) {
-    auto per_strip = [&](int h) { return (int)((((long)slots * h + strips - 1) / strips + h - 1) / h * h); };
-    c2 = std::max(0, ny - per_strip(h2));
-    c1 = std::max(0, c2 - per_strip(h1));
-  }
-  std::vector<Unit> units;
-  auto tier = [&](int r0, int r1, int h) {
-    for (int j = r0; j < r1; j += h)
-      for (int sx = 0; sx < ntx; ++sx) {
-        const int j1 = std::min(r1, j + h);
-        if (!wet_in(sx, j, j1)) continue;
-        Unit u{};
-        u.g = 0; u.sx = (int16_t)sx; u.j0 = j; u.rows = j1 - j; u.u = (int32_t)units.size();
-        units.push_back(u);
-      }
-  };
-  tier(0, c1, ty);
-  tier(c1, c2, h1);
-  tier(c2, ny, h2);
-  return units;
-}
-
 template <typename T>
 static int upload_planes(pcg_handle *h, DevPlanes<T> &P, cudaStream_t s) {
   const HostGrid &G = h->G;
@@ -218,8 +162,21 @@ static int upload_planes(pcg_handle *h, DevPlanes<T> &P, cudaStream_t s) {
   if (!P.ks.ok) { set_error("no kernel for this pattern / tile width"); return PCG_EINVAL; }
   int rc = prepare_set(P.ks);
   if (rc) return rc;
-  // units: rectangles of the strips holding a wet cell, claimed in list order
-  P.units = make_units(G, P.tx, P.ty, std::min(P.ks.ctas1, P.ks.ctas2), strip_rows(G, P.tx));
+  // units: strips holding a wet cell
+  const int nty = (G.ny + P.ty - 1) / P.ty;
+  P.units.clear();
+  for (int sy = 0; sy < nty; ++sy)
+    for (int sx = 0; sx < ntx; ++sx) {
+      bool any = false;
+      for (int j = sy * P.ty; j < std::min(G.ny, (sy + 1) * P.ty) && !any; ++j)
+        for (int i = sx * P.tx; i < std::min(G.nx, (sx + 1) * P.tx); ++i)
+          if (G.idx[(size_t)j * G.nx + i] >= 0) { any = true; break; }
+      if (any) {
+        Unit u{};
+        u.g = 0; u.sx = (int16_t)sx; u.sy = (int16_t)sy; u.u = (int32_t)P.units.size();
+        P.units.push_back(u);
+      }
+    }
   P.n_units = (int)P.units.size();
   const size_t nplanes = P.plane_count();
   const size_t bytes_planes = nplanes * P.plane_elems * sizeof(T);
@@ -376,8 +333,6 @@ int members_arm(LoopPlan &L, LaunchState *ls_host, int active, int max_launches,
   ls_host->t0_ns = 0;
   ls_host->timed_out = 0;
   ls_host->cond_cleared = 0;
-  ls_host->claim_next = 0;
-  ls_host->claim_exit = 0;
   const char *e = getenv("PCG_LOOP_BUDGET_S");
   const double budget_s = (e && atof(e) > 0) ? atof(e) : 300.0;
   ls_host->budget_ns = (uint64_t)(budget_s * 1e9);
@@ -913,38 +868,48 @@ static int choose_ty(int nx, int ny, int tx, int min_ty) {
 }
 
 // Strip height: the candidate that minimises a makespan model of one
-// iteration's two persistent launches over the grid's unit list (make_units:
-// full-height units, then the finer last tiers). The CTAs of a launch claim
-// units in list order, so the model assigns each unit to the CTA that frees
-// first; a launch lasts as long as its last CTA. A unit of h rows costs
-// h + 3 steps in k_stencil and h + 2 LD + 2 in k_precond (the pipeline depths)
-// plus UNIT_STEPS for its reduction and the refill of the stream; a k_precond
-// step weighs 1.5 k_stencil steps. Few units (small grids) make every CTA's
-// chain one short unit; many units make the sum over units, and the short
-// tail, decide.
+// iteration's two persistent launches over the grid's active units. CTA c of
+// a launch with G resident CTAs takes units c, c + G, ... (band-major order,
+// as upload_planes builds them); a launch lasts as long as its slowest CTA's
+// chain of steps. A unit of h rows costs h + 3 steps in k_stencil and
+// h + 2 LD + 2 in k_precond (the pipeline depths) plus UNIT_STEPS for its
+// reduction and the refill of the stream; a k_precond step weighs 1.5
+// k_stencil steps. Few units (small grids) make every CTA's chain one short
+// unit; many units make the count per CTA, and its rounding, decide.
+// Measured on 4322 x 3059 (three strip / precision pairs, 7 to 9 heights
+// each), 1442 x 1021, 722 x 511 and 182 x 149 (both precisions, 7 heights),
+// the model's height was the fastest one every time (up to 2.7x faster than
+// a fixed 64 rows for binary32 on small grids).
 static int model_ty(const HostGrid &G, int tx, const KernelSet &ks, int ld) {
   constexpr double UNIT_STEPS = 10.0;
-  static const int cand[] = {4, 8, 16, 24, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128, 160, 192, 256};
-  const std::vector<uint8_t> row_wet = strip_rows(G, tx);
+  static const int cand[] = {4, 8, 16, 24, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128};
+  const int ntx = (G.nx + tx - 1) / tx;
+  std::vector<uint8_t> row_wet((size_t)ntx * G.ny, 0);     // [strip][row]: any wet cell
+  for (int j = 0; j < G.ny; ++j)
+    for (int i = 0; i < G.nx; ++i)
+      if (G.idx[(size_t)j * G.nx + i] >= 0) row_wet[(size_t)(i / tx) * G.ny + j] = 1;
   const int g1 = std::max(ks.ctas1, 1), g2 = std::max(ks.ctas2, 1);
-  auto makespan = [](const std::vector<Unit> &units, int slots, double fixed) {
-    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
-    for (int c = 0; c < slots; ++c) free_at.push(0.0);
-    double end = 0.0;
-    for (const Unit &u : units) {
-      const double t = free_at.top() + u.rows + fixed;
-      free_at.pop();
-      free_at.push(t);
-      end = std::max(end, t);
-    }
-    return end;
-  };
+  std::vector<double> c1(g1), c2(g2);
   int best_ty = 128;
   double best = 1e300;
   for (int ty : cand) {
-    if ((G.ny + ty - 1) / ty > INT16_MAX) continue;    // row strips per column are limited like the columns
-    const std::vector<Unit> units = make_units(G, tx, ty, std::min(g1, g2), row_wet);
-    const double cost = makespan(units, g1, 3 + UNIT_STEPS) + 1.5 * makespan(units, g2, 2 * ld + 2 + UNIT_STEPS);
+    if ((G.ny + ty - 1) / ty > INT16_MAX) continue;    // strip coordinates are 16-bit
+    std::fill(c1.begin(), c1.end(), 0.0);
+    std::fill(c2.begin(), c2.end(), 0.0);
+    long k = 0;
+    const int nty = (G.ny + ty - 1) / ty;
+    for (int sy = 0; sy < nty; ++sy) {
+      const int j0 = sy * ty, j1 = std::min(G.ny, j0 + ty);
+      for (int sx = 0; sx < ntx; ++sx) {
+        bool any = false;
+        for (int j = j0; j < j1 && !any; ++j) any = row_wet[(size_t)sx * G.ny + j] != 0;
+        if (!any) continue;
+        c1[k % g1] += (j1 - j0) + 3 + UNIT_STEPS;
+        c2[k % g2] += (j1 - j0) + 2 * ld + 2 + UNIT_STEPS;
+        ++k;
+      }
+    }
+    const double cost = *std::max_element(c1.begin(), c1.end()) + 1.5 * *std::max_element(c2.begin(), c2.end());
     if (cost < best) { best = cost; best_ty = ty; }
     if (ty >= G.ny) break;                             // taller strips give the same units
   }
@@ -1118,7 +1083,6 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     rc = upload_planes(h.get(), h->p64, s);
     if (rc) { h->p64.release(); return rc; }
     if (cudaMalloc(&h->ls, sizeof(LaunchState)) != cudaSuccess) { cudaGetLastError(); h->p64.release(); set_error("device allocation failed"); return PCG_ENOMEM; }
-    CK(cudaMemsetAsync(h->ls, 0, sizeof(LaunchState), s));   // claim counters start at zero
     if (cudaMallocHost(&h->ls_host, sizeof(LaunchState)) != cudaSuccess ||
         cudaMallocHost(&h->st_host, sizeof(SolveState)) != cudaSuccess) {
       cudaGetLastError(); set_error("pinned allocation failed"); return PCG_ENOMEM;

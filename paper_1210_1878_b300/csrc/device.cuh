@@ -73,8 +73,6 @@ struct LaunchState {
   int32_t cond_cleared;    // the loop condition has been cleared in this launch
   int32_t bodies_total;    // loop-body executions over every pass of a solve (launch count)
   int32_t passes;          // outer passes of a solve (restarts / refinement steps + 1)
-  uint32_t claim_next;     // next unit of the running launch to hand out (0 between launches)
-  uint32_t claim_exit;     // CTAs of the running launch that have finished (0 between launches)
 };
 
 // A CUtensorMap as the kernels see it: 128 opaque bytes, 64-byte aligned.
@@ -111,11 +109,10 @@ struct GridDev {
   const TensorMapBytes *tm;   // [TM_COUNT] or null (one row per copy)
 };
 
-struct Unit {              // rows [j0, j0 + rows) of strip sx of one grid
+struct Unit {              // one strip of one grid
   int16_t g, sx;
-  int32_t j0;
-  int32_t u;               // index of the unit within its grid (its slot in the reduction order)
-  int32_t rows;
+  int16_t sy, pad;
+  int32_t u;               // index of the unit within its grid
 };
 
 struct KParams {
@@ -127,7 +124,7 @@ struct KParams {
   int32_t guard;           // 1 for the first stencil launch of the loop body
   int32_t dbg_skip_unit;   // test hook: unit whose first row copy is never issued (-1: none)
   uint64_t timeout_ns;     // bound on every mbarrier wait
-  int32_t n_units;         // units in the list; the persistent CTAs claim them one at a time
+  int32_t n_units;         // units in the list; CTAs stride over them (persistent)
   int32_t pad;
 };
 

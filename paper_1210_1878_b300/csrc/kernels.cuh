@@ -265,14 +265,8 @@ __device__ __forceinline__ void flag_timeout(SolveState *st) { atomicCAS(&st->st
 
 // ------------------------------------------------------------ row-group streaming
 // A CTA is TX compute threads plus one producer warp, and it is persistent:
-// its producer warp claims the launch's units one at a time from a counter in
-// the launch state (a CTA that finishes early takes more units: the list puts
-// large units first and small ones last, so the launch ends with short units
-// rather than with the CTAs that happened to hold one large unit more) and
-// hands each claimed unit to the compute threads through a small queue in
-// shared memory. Which CTA runs a unit does not change its result: partial
-// sums are kept per unit and added in unit order.
-// The producer streams the input fields of its units, unit after unit
+// it takes the units blockIdx.x, blockIdx.x + gridDim.x, ... of the launch's
+// list. The producer streams the input fields of its units, unit after unit
 // without a pause, in groups of RB consecutive rows into a ring of NSG group
 // slots. Lane f of the producer owns field f and issues one copy per group: a
 // 2D tensor tile of RB rows (cp.async.bulk.tensor) when RB > 1, a 1D bulk copy
@@ -284,9 +278,8 @@ __device__ __forceinline__ void flag_timeout(SolveState *st) { atomicCAS(&st->st
 // here (each occupies its issuing thread for a few hundred ns on this GPU), so
 // several rows per copy is what lets a few CTAs per SM keep HBM busy.
 
-// control words after the barriers, then the unit queue
-enum { CTL_ABORT = 0, CTL_ARMED = 1, CTL_SEEN = 2, CTL_FLAG = 3, CTL_PUB = 4, CTL_CONS = 5, CTL_CUR = 6 };
-constexpr int UQ = 16;            // unit queue entries (more than any ring's groups)
+// control words at the start of shared memory (after the barriers)
+enum { CTL_ABORT = 0, CTL_ARMED = 1, CTL_SEEN = 2, CTL_FLAG = 3 };
 
 struct FieldCopy {
   const char *src;      // RB = 1: element (first box column, row 0) of the plane, as bytes
@@ -346,81 +339,47 @@ __device__ __forceinline__ void compute_sync() {
   asm volatile("bar.sync 1, %0;" ::"r"(NC) : "memory");
 }
 
-// Wait until pred() holds, giving up after timeout_ns (one thread).
-template <class Pred>
-__device__ __forceinline__ bool spin_bounded(Pred pred, uint64_t timeout_ns) {
-  if (pred()) return true;
-  const uint64_t t0 = global_ns();
-  for (uint32_t it = 1;; ++it) {
-    if (pred()) return true;
-    if ((it & 63u) == 0 && global_ns() - t0 > timeout_ns) return false;
-  }
+// A CTA's next unit after unit ui when ui's whole grid is to be skipped
+// (done): the first index at or past u_end = u_off + n_units of that grid in
+// the CTA's stride. Units of a grid are contiguous in a launch's list.
+__device__ __forceinline__ int skip_grid(int ui, int u_end) {
+  const int g = (int)gridDim.x;
+  return u_end <= ui ? ui + g : ui + (u_end - ui + g - 1) / g * g;
 }
 
-// The producer warp's loop. Lane 0 claims the next unit of the launch; a unit
-// whose grid is to be skipped (setup returns false, with u_end the end of
-// that grid's units) pushes the claim counter past the grid's remaining units
-// and is not handed on. Every other claimed unit is appended to the unit
-// queue (uq, published count ctl[CTL_PUB]); then lane f issues the copies of
-// field f of every group of the unit, in order. setup(ui, f, c, has, mlo, ng,
-// u_end) describes unit ui's field f. Once the CTA is aborting, units are
-// still handed on (so that the compute threads join every unit's reduction)
-// but no copy is issued. Ends the queue with -1. Returns the number of groups
-// armed.
+// The producer warp's loop: lane f issues the copies of field f of every
+// group of the CTA's units, in order. setup(ui, f, c, has, mlo, ng, u_end)
+// describes unit ui's field f (returns false when ui's grid is to be skipped,
+// with u_end the end of that grid's units). Returns the number of groups
+// armed; stops early once the CTA is aborting.
 template <int NSG, int RB, class Setup>
 __device__ __forceinline__ uint32_t produce_all(const KParams &p, unsigned char *ring, int group_bytes, uint64_t *full,
-                                                uint64_t *empty, volatile int *ctl, volatile int *uq, Setup setup) {
+                                                uint64_t *empty, volatile int *ctl, Setup setup) {
   const int lane = threadIdx.x & 31;
   uint32_t gq = 0;
-  int last_g = -1, pub = 0;
-  bool stopped = false;                      // no more copies: the CTA is aborting
-  // append v to the unit queue once there is room (bounded wait); false: gave up
-  auto publish = [&](int v) -> bool {
-    bool ok = true;
-    if (lane == 0) {
-      ok = spin_bounded([&] { return pub - ctl[CTL_CONS] < UQ; }, p.timeout_ns);
-      if (ok) {
-        uq[pub % UQ] = v;
-        __threadfence_block();
-        ctl[CTL_PUB] = pub + 1;
-      } else {
-        ctl[CTL_ABORT] = 1;
-      }
-    }
-    ++pub;
-    return __shfl_sync(0xffffffffu, ok, 0);
-  };
-  for (;;) {
-    int ui = 0;
-    if (lane == 0) ui = (int)atomicAdd(&p.ls->claim_next, 1u);
-    ui = __shfl_sync(0xffffffffu, ui, 0);
-    if (ui >= p.n_units) break;
+  int last_g = -1;
+  for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
     FieldCopy c{};
     bool has = false;
     int mlo = 0, ng = 0, u_end = 0;
-    const bool keep = __shfl_sync(0xffffffffu, setup(ui, lane, c, has, mlo, ng, u_end), 0);
-    if (!keep) {
-      if (lane == 0 && u_end > ui + 1) atomicMax(&p.ls->claim_next, (unsigned)u_end);
+    if (!setup(ui, lane, c, has, mlo, ng, u_end)) {
+      ui = skip_grid(ui, u_end) - (int)gridDim.x;
       continue;
     }
-    if (!publish(ui)) return gq;             // the compute threads stopped taking units
-    stopped = __shfl_sync(0xffffffffu, stopped || ctl[CTL_ABORT] != 0, 0);
-    if (stopped) continue;
     const int g_un = p.units[ui].g;
     const bool skip_first = (p.dbg_skip_unit == ui) && lane == 0;
     if constexpr (RB > 1)
       if (has && g_un != last_g) tensormap_acquire(c.tmap);
     last_g = g_un;
     const uint32_t total = __reduce_add_sync(0xffffffffu, has ? c.bytes : 0u);
-    for (int q = 0; q < ng; ++q) {
+    for (int q = 0; q < ng; ++q, ++gq) {
       const uint32_t slot = gq % NSG, fill = gq / NSG;
       if (fill > 0) {
         bool ok = true;
         if (lane == 0) ok = mbar_wait_or_abort(&empty[slot], (fill - 1) & 1u, p.timeout_ns, &ctl[CTL_ABORT]);
         if (!__shfl_sync(0xffffffffu, ok, 0)) {
           if (lane == 0) ctl[CTL_ABORT] = 1;
-          stopped = true;
-          break;
+          return gq;
         }
       }
       if (lane == 0) mbar_arrive_expect_tx(&full[slot], total);
@@ -432,59 +391,24 @@ __device__ __forceinline__ uint32_t produce_all(const KParams &p, unsigned char 
         if constexpr (RB == 1) bulk_g2s(dst, c.src + (ptrdiff_t)m0 * c.pitch_b, c.bytes, &full[slot]);
         else tma_2d_g2s(dst, c.tmap, c.x, m0 + GY, &full[slot]);
       }
-      ++gq;
     }
   }
-  publish(-1);
   return gq;
 }
 
-// The compute threads' next unit from the queue (-1: none left, or the
-// producer could not be waited for). Thread 0 waits for it and passes it on
-// through ctl[CTL_CUR]; k counts the units taken so far.
-template <int NC>
-__device__ __forceinline__ int next_unit(volatile int *ctl, const volatile int *uq, int k, uint64_t timeout_ns) {
-  if (threadIdx.x == 0) {
-    const bool ok = spin_bounded([&] { return ctl[CTL_PUB] > k; }, timeout_ns);
-    ctl[CTL_CUR] = ok ? uq[k % UQ] : -1;
-    if (!ok) ctl[CTL_ABORT] = 1;
-  }
-  compute_sync<NC>();
-  const int ui = ctl[CTL_CUR];
-  compute_sync<NC>();
-  if (threadIdx.x == 0) ctl[CTL_CONS] = k + 1;
-  return ui;
-}
-
-// End of a launch: the last CTA to leave resets the claim counters for the
-// next launch (every CTA has finished claiming by then).
-__device__ __forceinline__ void launch_exit(LaunchState *ls) {
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(&ls->claim_exit, 1u) + 1u == gridDim.x) {
-      ls->claim_next = 0u;
-      ls->claim_exit = 0u;
-      __threadfence();
-    }
-  }
-}
-
-// Shared memory: barriers (bytes 0..191), control words (192..255), the unit
-// queue (256..319), then the group ring from byte 384.
-constexpr int RING_OFF = 384;
+// Shared-memory geometry common to both kernels: barriers and control words
+// in the first 256 bytes of a 128-byte aligned base, then the group ring.
 template <int NSG>
 struct RingCtl {
   static_assert(NSG <= 12, "barrier area");
   uint64_t *full, *empty;
   volatile int *ctl;
-  volatile int *uq;
   unsigned char *ring;
   __device__ __forceinline__ explicit RingCtl(unsigned char *base) {
     full = reinterpret_cast<uint64_t *>(base);
     empty = full + NSG;
     ctl = reinterpret_cast<volatile int *>(base + 192);
-    uq = reinterpret_cast<volatile int *>(base + 256);
-    ring = base + RING_OFF;
+    ring = base + 256;
   }
 };
 
@@ -591,7 +515,7 @@ struct K1Geom {
   // kernel cover its TX + 2R columns with whole warps, no extra pass)
   static constexpr int NCG = round_up_c(TX, 32);
   static constexpr int NGRP = 1, NC = NGRP * NCG, NT = NC + 32;
-  static constexpr size_t SMEM = 128 + RING_OFF + (size_t)NSG * GROUP + sizeof(T) * (size_t)NDN * WDN + 16 * (NT / 32) + 64;
+  static constexpr size_t SMEM = 128 + 256 + (size_t)NSG * GROUP + sizeof(T) * (size_t)NDN * WDN + 16 * (NT / 32) + 64;
 };
 
 // Compile-time row bookkeeping of the unrolled step loops: floor division
@@ -805,7 +729,6 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
   if (tid == 0) {
     for (int s = 0; s < G::NSG; ++s) { mbar_init(&rc.full[s], 1); mbar_init(&rc.empty[s], 1); }
     rc.ctl[CTL_ABORT] = 0; rc.ctl[CTL_ARMED] = 0; rc.ctl[CTL_SEEN] = 0; rc.ctl[CTL_FLAG] = 0;
-    rc.ctl[CTL_PUB] = 0; rc.ctl[CTL_CONS] = 0; rc.ctl[CTL_CUR] = 0;
     fence_mbar_init();
   }
   __syncthreads();
@@ -823,8 +746,8 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
       u_end = gdp->u_off + gdp->n_units;
       if (skip_unit(gdp->st)) return false;
-      const int i0 = un.sx * TX, j0 = un.j0;
-      const int mhi = j0 + un.rows;
+      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
+      const int mhi = min(j0 + gdp->ty, gdp->ny);
       mlo = j0 - 1;
       ng = (mhi - mlo + G::RB) / G::RB;
       const int dsel = gdp->st->dsel;
@@ -853,21 +776,23 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
       return true;
     };
     const uint32_t gq =
-        produce_all<G::NSG, G::RB>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, rc.uq, setup);
+        produce_all<G::NSG, G::RB>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, setup);
     if (tid == G::NC) rc.ctl[CTL_ARMED] = (int)gq;
   } else {
-    // ---- compute threads: the units the producer hands on, in its order
+    // ---- compute threads
     uint32_t gbase = 0, seen = 0;
     bool aborted = false;
-    for (int k = 0;; ++k) {
-      const int ui = next_unit<G::NC>(rc.ctl, rc.uq, k, p.timeout_ns);
-      if (ui < 0) break;
+    for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
       const Unit un = p.units[ui];
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
       SolveState *st = gdp->st;
+      if (skip_unit(st)) {
+        ui = skip_grid(ui, gdp->u_off + gdp->n_units) - (int)gridDim.x;
+        continue;
+      }
       const int nx = gdp->nx, ny = gdp->ny;
-      const int i0 = un.sx * TX, j0 = un.j0;
-      const int rend = j0 + un.rows;
+      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
+      const int rend = min(j0 + gdp->ty, ny);
       const int mlo = j0 - 1, mhi = rend;
       const int ng = (mhi - mlo + G::RB) / G::RB;
       double acc0 = 0.0, acc1 = 0.0;
@@ -919,7 +844,6 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
   }
   __syncthreads();
   drain_groups<G::NSG>(rc, p.timeout_ns);
-  launch_exit(ls);
 }
 
 // ------------------------------------------------------------ kernel 2
@@ -956,7 +880,7 @@ struct K2Geom {
   // faster than 1 on this GPU), then the producer warp
   static constexpr int NCG = round_up_c(TX, 32);      // compute threads of a group (whole warps)
   static constexpr int NGRP = 1, NC = NGRP * NCG, NT = NC + 32;
-  static constexpr size_t SMEM = 128 + RING_OFF + (size_t)NSG * GROUP +
+  static constexpr size_t SMEM = 128 + 256 + (size_t)NSG * GROUP +
                                  sizeof(T) * ((size_t)NRN * WRC + (size_t)NTT * WTC) + 16 * (NT / 32) + 64;
 };
 
@@ -1161,7 +1085,6 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
   if (tid == 0) {
     for (int s = 0; s < G::NSG; ++s) { mbar_init(&rc.full[s], 1); mbar_init(&rc.empty[s], 1); }
     rc.ctl[CTL_ABORT] = 0; rc.ctl[CTL_ARMED] = 0; rc.ctl[CTL_SEEN] = 0; rc.ctl[CTL_FLAG] = 0;
-    rc.ctl[CTL_PUB] = 0; rc.ctl[CTL_CONS] = 0; rc.ctl[CTL_CUR] = 0;
     fence_mbar_init();
   }
   __syncthreads();
@@ -1177,8 +1100,8 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
       u_end = gdp->u_off + gdp->n_units;
       if (skip_unit(gdp->st)) return false;
-      const int i0 = un.sx * TX, j0 = un.j0;
-      const int rend = j0 + un.rows;
+      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
+      const int rend = min(j0 + gdp->ty, gdp->ny);
       const int mhi = rend + LD - 1;
       mlo = j0 - LD;
       ng = (mhi - mlo + G::RB) / G::RB;
@@ -1201,21 +1124,23 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
       return true;
     };
     const uint32_t gq =
-        produce_all<G::NSG, G::RB>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, rc.uq, setup);
+        produce_all<G::NSG, G::RB>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, setup);
     if (tid == G::NC) rc.ctl[CTL_ARMED] = (int)gq;
   } else {
-    // ---- compute threads: the units the producer hands on, in its order
+    // ---- compute threads
     uint32_t gbase = 0, seen = 0;
     bool aborted = false;
-    for (int k = 0;; ++k) {
-      const int ui = next_unit<G::NC>(rc.ctl, rc.uq, k, p.timeout_ns);
-      if (ui < 0) break;
+    for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
       const Unit un = p.units[ui];
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
       SolveState *st = gdp->st;
+      if (skip_unit(st)) {
+        ui = skip_grid(ui, gdp->u_off + gdp->n_units) - (int)gridDim.x;
+        continue;
+      }
       const int nx = gdp->nx, ny = gdp->ny;
-      const int i0 = un.sx * TX, j0 = un.j0;
-      const int rend = j0 + un.rows;
+      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
+      const int rend = min(j0 + gdp->ty, ny);
       const int mlo = j0 - LD, mhi = rend + LD - 1;
       const int ng = (mhi - mlo + G::RB) / G::RB;
       double acc0 = 0.0, acc1 = 0.0;
@@ -1269,7 +1194,6 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
   }
   __syncthreads();
   drain_groups<G::NSG>(rc, p.timeout_ns);
-  launch_exit(ls);
 }
 
 // ------------------------------------------------------------ small kernels
@@ -1281,7 +1205,7 @@ __global__ void __launch_bounds__(TX) k_finalize(KParams p) {
   SolveState *st = gd.st;
   if (*(volatile int32_t *)&st->retired) return;
   const int col = un.sx * TX + threadIdx.x;
-  const int j0 = un.j0, rend = j0 + un.rows;
+  const int j0 = un.sy * gd.ty, rend = min(j0 + gd.ty, gd.ny);
   const T pend = (T)st->pending;
   const bool zero = st->bzero != 0;
   const T *d = gd.d[st->dsel];
@@ -1301,7 +1225,7 @@ __global__ void __launch_bounds__(TX) k_pack(KParams p, const U *user, int which
   const GridDev<T> &gd = reinterpret_cast<const GridDev<T> *>(p.grids)[un.g];
   T *dst = which == 0 ? const_cast<T *>(gd.b) : which == 1 ? gd.x : which == 2 ? gd.r[0] : gd.d[0];
   const int col = un.sx * TX + threadIdx.x;
-  const int j0 = un.j0, rend = j0 + un.rows;
+  const int j0 = un.sy * gd.ty, rend = min(j0 + gd.ty, gd.ny);
   if (col < gd.nx) {
     for (int r = j0; r < rend; ++r) {
       const size_t ro = (size_t)r * gd.pitch;
@@ -1325,7 +1249,7 @@ static __global__ void k_residual_to_f32(const GridDev<double> *g64, const GridD
   const GridDev<float> &f = g32[un.g];
   if (*(volatile int32_t *)&a.st->retired) return;
   const int col = un.sx * TX + threadIdx.x;
-  const int j0 = un.j0, rend = j0 + un.rows;
+  const int j0 = un.sy * a.ty, rend = min(j0 + a.ty, a.ny);
   const double *r = a.r[a.st->rsel];
   const double sc = scale != 0.0 ? scale : a.st->scale;
   float *b = const_cast<float *>(f.b);
@@ -1351,7 +1275,7 @@ static __global__ void k_correct_f64(const GridDev<double> *g64, const GridDev<f
   const GridDev<float> &f = g32[un.g];
   if (*(volatile int32_t *)&a.st->retired || *(volatile int32_t *)&f.st->retired) return;
   const int col = un.sx * TX + threadIdx.x;
-  const int j0 = un.j0, rend = j0 + un.rows;
+  const int j0 = un.sy * a.ty, rend = min(j0 + a.ty, a.ny);
   const double inv = inv_scale != 0.0 ? inv_scale : 1.0 / a.st->scale;
   if (col < a.nx)
     for (int j = j0; j < rend; ++j) {

@@ -346,7 +346,6 @@ int solver_server_create(const pcg_server_opts *opts, pcg_server **out) {
   if (s->opts.chunk_iters <= 0) s->opts.chunk_iters = 16;
   CK(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
   CK(cudaMalloc(&s->ls_dev, sizeof(LaunchState)));
-  CK(cudaMemset(s->ls_dev, 0, sizeof(LaunchState)));
   CK(cudaMallocHost(&s->ls_host, sizeof(LaunchState)));
   pcg_server *raw = s.release();
   raw->th = std::thread([raw] { raw->run(); });
