@@ -138,10 +138,18 @@ __device__ __forceinline__ double to_f64(float v) {
 }
 
 // Dot-product term accumulation. binary64 kernels accumulate in binary64.
-// binary32 kernels keep a binary32 partial sum per thread over the rows of
-// its column in one work unit (at most a unit's height of terms); the partial
-// is widened exactly and added into the binary64 accumulator when the unit is
-// done, so every long accumulation is in binary64.
+// binary32 kernels (the inner solves of the mixed mode) take every product
+// exactly and sum it with a compensated summation, entirely in the binary32
+// pipe: Dot2 of Ogita, Rump and Oishi ("Accurate sum and dot product", SIAM
+// J. Sci. Comput. 26, 2005). The product a*b is split into p + e exactly
+// (p = fl(a*b), e = fma(a, b, -p)); p is added to the running sum s by
+// Knuth's TwoSum, whose exact rounding error joins e in a separate binary32
+// error sum c. At the end of a unit the thread's s and c are widened exactly
+// and added in binary64, and the units' partials are summed in binary64: the
+// result is as accurate as a dot product of the exact products carried in
+// twice the binary32 precision, with no binary64 arithmetic per point (the
+// FP64 pipe of this GPU is 64 times slower than the FP32 one). The _rn
+// intrinsics keep the compiler from contracting or reassociating the steps.
 template <typename T>
 struct DotAcc;
 template <>
@@ -152,9 +160,17 @@ struct DotAcc<double> {
 };
 template <>
 struct DotAcc<float> {
-  float v = 0.0f;
-  __device__ __forceinline__ void add(float a, float b) { v = fmaf(a, b, v); }
-  __device__ __forceinline__ double total() const { return to_f64(v); }
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    const float t = __fadd_rn(s, p);
+    const float bv = __fsub_rn(t, s);
+    const float z = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(z, e));
+  }
+  __device__ __forceinline__ double total() const { return to_f64(s) + to_f64(c); }
 };
 
 // ------------------------------------------------------------ stores
