@@ -306,6 +306,47 @@ void pcg_free(pcg_handle *h);
 const char *pcg_status_string(int status);
 const char *pcg_last_error_message(void);
 
+/* --------------------------------------------------- row-band sharding */
+
+/* The layout in which one large grid is split over several GPUs: contiguous
+ * bands of rows of about equal wet count. The paper has no counterpart (it runs
+ * one GPU); the iteration is Algorithm 1 unchanged, whose two reductions per
+ * iteration become the only global steps besides the exchange of band-edge
+ * rows. pcg_band_plan computes the bands of a mask on the host: row0[b] ..
+ * row0[b + 1] - 1 are band b's rows (row0 has nbands + 1 entries, row0[0] = 0,
+ * row0[nbands] = ny), each band at least *halo rows tall; *halo is the number of
+ * a neighbour's rows a band reads: max(1, LD) with LD = 2 for
+ * PCG_PAT_TRIL_A2, 1 for PCG_PAT_TRIL_A, 0 otherwise. Errors: PCG_EINVAL (NULL
+ * argument, nbands < 1, or fewer than nbands * halo rows). */
+int pcg_band_plan(int32_t nx, int32_t ny, const uint8_t *wet, int32_t pattern, int32_t nbands, int32_t *row0,
+                  int32_t *halo);
+
+typedef struct pcg_shard pcg_shard;
+
+/* Split the grid of h (binary64 planes) into nbands >= 2 bands on the current
+ * GPU: each band gets planes for its rows and *halo rows of each neighbour,
+ * with A, Z and D^-1 taken from h's factor (built once for the whole grid),
+ * and every kernel of the solve runs over all bands' own rows in one launch,
+ * sharing one reduction state (on several GPUs these would be per-rank
+ * partial sums and two allreduces per iteration). The rows a band reads from
+ * a neighbour are refreshed by an exchange kernel after the kernel that wrote
+ * them (on several GPUs: sends and receives of the same row blocks). h must
+ * outlive the shard and not be retiled while it exists. Errors: PCG_EINVAL,
+ * PCG_ENOMEM, PCG_ECUDA. */
+int pcg_shard_create(pcg_handle *h, int32_t nbands, void *cuda_stream, pcg_shard **out);
+
+/* The bands of a shard: *nbands, row0[nbands + 1] and *halo (any may be NULL). */
+int pcg_shard_bands(const pcg_shard *sh, int32_t *nbands, int32_t *row0, int32_t *halo);
+
+/* Solve A x = b over the bands (binary64, Algorithm 1 with the true-residual
+ * check and restarts decided on the device, as pcg_solve). b and x are device
+ * pointers, [ny][nx] binary64 (x read as x0 when opts->use_x0). Synchronises
+ * cuda_stream; returns the solve status and fills stats (may be NULL). */
+int pcg_shard_solve(pcg_shard *sh, const double *b, double *x, const pcg_opts *opts, pcg_stats *stats,
+                    void *cuda_stream);
+
+void pcg_shard_free(pcg_shard *sh);
+
 /* ---------------------------------------------------------------- serving */
 
 typedef struct {

@@ -29,7 +29,8 @@ EXPORTED = [
     "pcg_apply_f32", "pcg_autotune", "pcg_tiles",
     "pcg_ainv_export", "pcg_resident_bytes", "pcg_n_wet", "pcg_free", "pcg_status_string",
     "pcg_last_error_message", "pcg_debug_wait_timeout", "pcg_profile_kernels", "pcg_kernel_launches",
-    "pcg_fp64_fma_rate", "solver_server_create", "solver_server_register", "solver_server_submit",
+    "pcg_fp64_fma_rate", "pcg_band_plan", "pcg_shard_create", "pcg_shard_bands", "pcg_shard_solve",
+    "pcg_shard_free", "solver_server_create", "solver_server_register", "solver_server_submit",
     "solver_server_wait", "solver_server_cancel", "solver_server_stats", "solver_server_destroy",
 ]
 
@@ -105,6 +106,11 @@ def _load():
         "pcg_profile_kernels": (C.c_int, [vp, vp, i32, i32, C.POINTER(dbl), C.POINTER(dbl), vp]),
         "pcg_kernel_launches": (C.c_uint64, []),
         "pcg_fp64_fma_rate": (C.c_int, [i32, C.POINTER(dbl), C.POINTER(dbl), vp]),
+        "pcg_band_plan": (C.c_int, [i32, i32, vp, i32, i32, vp, C.POINTER(i32)]),
+        "pcg_shard_create": (C.c_int, [vp, i32, vp, C.POINTER(vp)]),
+        "pcg_shard_bands": (C.c_int, [vp, C.POINTER(i32), vp, C.POINTER(i32)]),
+        "pcg_shard_solve": (C.c_int, [vp, vp, vp, C.POINTER(pcg_opts), C.POINTER(pcg_stats), vp]),
+        "pcg_shard_free": (None, [vp]),
         "solver_server_create": (C.c_int, [C.POINTER(pcg_server_opts), C.POINTER(vp)]),
         "solver_server_register": (C.c_int, [vp, vp, C.POINTER(i32)]),
         "solver_server_submit": (C.c_int, [vp, i32, vp, vp, i32, DONE_CB, vp, C.POINTER(C.c_uint64)]),
@@ -362,6 +368,59 @@ def pcg_fp64_fma_rate(launches=10, stream=None):
 
 def pcg_kernel_launches() -> int:
     return int(lib.pcg_kernel_launches())
+
+
+# ------------------------------------------------------------ row-band sharding
+def pcg_band_plan(wet, pattern=PCG_PAT_TRIL_A2, nbands=2):
+    """Row bands of about equal wet count: (row0 [nbands + 1], halo rows)."""
+    w = np.ascontiguousarray(wet, dtype=np.uint8)
+    ny, nx = w.shape
+    row0 = np.zeros(int(nbands) + 1, np.int32)
+    halo = C.c_int32()
+    rc = lib.pcg_band_plan(int(nx), int(ny), w.ctypes.data, int(pattern), int(nbands), row0.ctypes.data, C.byref(halo))
+    if rc != PCG_OK:
+        raise PCGError(rc, "pcg_band_plan")
+    return row0, halo.value
+
+
+class Shard:
+    """A grid split into row bands on the current GPU (pcg_shard_*)."""
+
+    def __init__(self, h: Handle, nbands=2, stream=None):
+        out = C.c_void_p()
+        rc = lib.pcg_shard_create(h.ptr, int(nbands), _stream(stream), C.byref(out))
+        if rc != PCG_OK:
+            raise PCGError(rc, "pcg_shard_create")
+        self._s = out
+        self._h = h                 # the whole grid must outlive the shard
+
+    def bands(self):
+        n = C.c_int32()
+        lib.pcg_shard_bands(self._s, C.byref(n), None, None)
+        row0 = np.zeros(n.value + 1, np.int32)
+        halo = C.c_int32()
+        lib.pcg_shard_bands(self._s, None, row0.ctypes.data, C.byref(halo))
+        return row0, halo.value
+
+    def solve(self, b, x, opts: pcg_opts | None = None, stream=None, check=True) -> pcg_stats:
+        st = pcg_stats()
+        o = opts if opts is not None else make_opts()
+        rc = lib.pcg_shard_solve(self._s, _ptr(b), _ptr(x), C.byref(o), C.byref(st), _stream(stream))
+        if check and rc != PCG_OK:
+            raise PCGError(rc, "pcg_shard_solve")
+        st.rc = rc
+        return st
+
+    def close(self):
+        if self._s and self._s.value:
+            lib.pcg_shard_free(self._s)
+            self._s = C.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # -------------------------------------------------------------------- serving

@@ -18,10 +18,10 @@ ROOT = os.path.dirname(HERE)
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["api.cu", "solve.cu", "server.cu", "noalloc.cu", "measure.cu", "kernels_f64_64.cu", "kernels_f64_128.cu",
+CU_SOURCES = ["api.cu", "solve.cu", "shard.cu", "server.cu", "noalloc.cu", "measure.cu", "kernels_f64_64.cu", "kernels_f64_128.cu",
               "kernels_f32_64.cu", "kernels_f32_128.cu", "kernels_exact.cu", "kernels_f64_wide.cu"]
 CPP_SOURCES = ["ainv_host.cpp"]
-HEADERS = ["pcg_internal.h", "device.cuh", "kernels.cuh", "handle.cuh", "kernel_table.cuh"]
+HEADERS = ["pcg_internal.h", "device.cuh", "kernels.cuh", "handle.cuh", "kernel_table.cuh", "solve_graph.cuh"]
 
 
 def _sources():

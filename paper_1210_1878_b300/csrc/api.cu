@@ -229,6 +229,7 @@ static int upload_planes(pcg_handle *h, DevPlanes<T> &P, cudaStream_t s) {
   gd.d[0] = P.plane(P.vec(5)); gd.d[1] = P.plane(P.vec(6));
   gd.b = P.plane(P.vec(7));
   gd.partial = P.partial; gd.st = P.st;
+  gd.row_off = 0; gd.own0 = 0; gd.own1 = G.ny;
   if ((rc = upload_tensor_maps(P))) return rc;
   gd.tm = P.tm;
   CK(cudaMemcpy(P.gd_dev, &gd, sizeof(gd), cudaMemcpyHostToDevice));
@@ -409,6 +410,8 @@ static int unpack_user(pcg_handle *h, DevPlanes<T> &P, double *user, int which, 
   if (!dev) CK(cudaMemcpyAsync(user, h->stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   return PCG_OK;
 }
+
+int upload_planes64(pcg_handle *h, cudaStream_t s) { return upload_planes<double>(h, h->p64, s); }
 
 int plan_single(pcg_handle *h) {
   if (h->plan64) return PCG_OK;

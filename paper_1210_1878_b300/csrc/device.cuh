@@ -107,6 +107,10 @@ struct GridDev {
   double *partial;         // [n_units][2]
   SolveState *st;
   const TensorMapBytes *tm;   // [TM_COUNT] or null (one row per copy)
+  // A row band of a larger grid (sharded solve): local row j is row j + row_off
+  // of the caller's [ny][nx] vectors, and rows [own0, own1) are the band's own
+  // (the others are halo rows filled by the exchange). A whole grid: 0, 0, ny.
+  int32_t row_off, own0, own1, pad2;
 };
 
 struct Unit {              // one strip of one grid

@@ -235,6 +235,7 @@ bool member_decide(Member &m, const pcg_opts &o, bool overrun, cudaStream_t s, i
 int member_store(Member &m, cudaStream_t s);                                      // unpack x
 void member_stats(Member &m);
 int plan_single(pcg_handle *h);                                                   // h->plan64
+int upload_planes64(pcg_handle *h, cudaStream_t s);   // h->p64 from h->G, h->F, h->tx, h->ty
 int ensure_f32(pcg_handle *h, cudaStream_t s);                                     // h->p32, h->plan32
 int plan_build32(LoopPlan &L, pcg_handle *const *hs, int n, bool with_graph, LaunchState *ls, cudaStream_t s);
 int solve_members_mixed(LoopPlan &L64, LoopPlan &L32, LaunchState *ls_host, std::vector<Member> &M,

@@ -762,8 +762,8 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
       u_end = gdp->u_off + gdp->n_units;
       if (skip_unit(gdp->st)) return false;
-      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
-      const int mhi = min(j0 + gdp->ty, gdp->ny);
+      const int i0 = un.sx * TX, j0 = gdp->own0 + un.sy * gdp->ty;
+      const int mhi = min(j0 + gdp->ty, gdp->own1);
       mlo = j0 - 1;
       ng = (mhi - mlo + G::RB) / G::RB;
       const int dsel = gdp->st->dsel;
@@ -807,8 +807,8 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
         continue;
       }
       const int nx = gdp->nx, ny = gdp->ny;
-      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
-      const int rend = min(j0 + gdp->ty, ny);
+      const int i0 = un.sx * TX, j0 = gdp->own0 + un.sy * gdp->ty;
+      const int rend = min(j0 + gdp->ty, gdp->own1);
       const int mlo = j0 - 1, mhi = rend;
       const int ng = (mhi - mlo + G::RB) / G::RB;
       double acc0 = 0.0, acc1 = 0.0;
@@ -1116,8 +1116,8 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
       u_end = gdp->u_off + gdp->n_units;
       if (skip_unit(gdp->st)) return false;
-      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
-      const int rend = min(j0 + gdp->ty, gdp->ny);
+      const int i0 = un.sx * TX, j0 = gdp->own0 + un.sy * gdp->ty;
+      const int rend = min(j0 + gdp->ty, gdp->own1);
       const int mhi = rend + LD - 1;
       mlo = j0 - LD;
       ng = (mhi - mlo + G::RB) / G::RB;
@@ -1155,8 +1155,8 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
         continue;
       }
       const int nx = gdp->nx, ny = gdp->ny;
-      const int i0 = un.sx * TX, j0 = un.sy * gdp->ty;
-      const int rend = min(j0 + gdp->ty, ny);
+      const int i0 = un.sx * TX, j0 = gdp->own0 + un.sy * gdp->ty;
+      const int rend = min(j0 + gdp->ty, gdp->own1);
       const int mlo = j0 - LD, mhi = rend + LD - 1;
       const int ng = (mhi - mlo + G::RB) / G::RB;
       double acc0 = 0.0, acc1 = 0.0;
@@ -1221,7 +1221,7 @@ __global__ void __launch_bounds__(TX) k_finalize(KParams p) {
   SolveState *st = gd.st;
   if (*(volatile int32_t *)&st->retired) return;
   const int col = un.sx * TX + threadIdx.x;
-  const int j0 = un.sy * gd.ty, rend = min(j0 + gd.ty, gd.ny);
+  const int j0 = gd.own0 + un.sy * gd.ty, rend = min(j0 + gd.ty, gd.own1);
   const T pend = (T)st->pending;
   const bool zero = st->bzero != 0;
   const T *d = gd.d[st->dsel];
@@ -1241,11 +1241,11 @@ __global__ void __launch_bounds__(TX) k_pack(KParams p, const U *user, int which
   const GridDev<T> &gd = reinterpret_cast<const GridDev<T> *>(p.grids)[un.g];
   T *dst = which == 0 ? const_cast<T *>(gd.b) : which == 1 ? gd.x : which == 2 ? gd.r[0] : gd.d[0];
   const int col = un.sx * TX + threadIdx.x;
-  const int j0 = un.sy * gd.ty, rend = min(j0 + gd.ty, gd.ny);
+  const int j0 = gd.own0 + un.sy * gd.ty, rend = min(j0 + gd.ty, gd.own1);
   if (col < gd.nx) {
     for (int r = j0; r < rend; ++r) {
       const size_t ro = (size_t)r * gd.pitch;
-      const T v = gd.a[ro + col] > (T)0 ? (T)user[(size_t)r * gd.nx + col] : (T)0;
+      const T v = gd.a[ro + col] > (T)0 ? (T)user[(size_t)(r + gd.row_off) * gd.nx + col] : (T)0;
       store_dup(dst + ro, col, gd.nx, v);
     }
   }
@@ -1265,7 +1265,7 @@ static __global__ void k_residual_to_f32(const GridDev<double> *g64, const GridD
   const GridDev<float> &f = g32[un.g];
   if (*(volatile int32_t *)&a.st->retired) return;
   const int col = un.sx * TX + threadIdx.x;
-  const int j0 = un.sy * a.ty, rend = min(j0 + a.ty, a.ny);
+  const int j0 = a.own0 + un.sy * a.ty, rend = min(j0 + a.ty, a.own1);
   const double *r = a.r[a.st->rsel];
   const double sc = scale != 0.0 ? scale : a.st->scale;
   float *b = const_cast<float *>(f.b);
@@ -1291,7 +1291,7 @@ static __global__ void k_correct_f64(const GridDev<double> *g64, const GridDev<f
   const GridDev<float> &f = g32[un.g];
   if (*(volatile int32_t *)&a.st->retired || *(volatile int32_t *)&f.st->retired) return;
   const int col = un.sx * TX + threadIdx.x;
-  const int j0 = un.sy * a.ty, rend = min(j0 + a.ty, a.ny);
+  const int j0 = a.own0 + un.sy * a.ty, rend = min(j0 + a.ty, a.own1);
   const double inv = inv_scale != 0.0 ? inv_scale : 1.0 / a.st->scale;
   if (col < a.nx)
     for (int j = j0; j < rend; ++j) {
@@ -1307,11 +1307,12 @@ __global__ void k_unpack(const GridDev<T> *gdp, U *user, int which) {
   const T *srcp = which == 0 ? gd.x : which == 1 ? gd.s : which == 2 ? gd.q : gd.r[0];
   // the solution of b = 0 is x = 0 whatever the x plane holds
   const bool zero = which == 0 && gd.st->bzero != 0;
-  const size_t n = (size_t)gd.nx * gd.ny;
+  // the own rows only (all rows of a whole grid)
+  const size_t n = (size_t)gd.nx * (size_t)(gd.own1 - gd.own0);
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(e / gd.nx), i = (int)(e % gd.nx);
+    const int j = gd.own0 + (int)(e / gd.nx), i = (int)(e % gd.nx);
     const size_t o = (size_t)j * gd.pitch + i;
-    user[e] = (gd.a[o] > (T)0 && !zero) ? (U)srcp[o] : (U)0;
+    user[(size_t)(j + gd.row_off) * gd.nx + i] = (gd.a[o] > (T)0 && !zero) ? (U)srcp[o] : (U)0;
   }
 }
 

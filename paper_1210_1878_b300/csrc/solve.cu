@@ -37,16 +37,12 @@
 #include <string>
 #include <vector>
 
-#include "handle.cuh"
+#include "solve_graph.cuh"
 
 namespace pcg {
 
-namespace {
 
-constexpr int CTL_THREADS = 256;
-constexpr int MAX_PASSES = 1024;   // runaway guard of the outer loop
-
-__device__ __forceinline__ int block_or(int v) { return __syncthreads_or(v); }
+static __device__ __forceinline__ int block_or(int v) { return __syncthreads_or(v); }
 
 // Solve set-up, replacing the host-written state: every member starts from
 // iteration 0 with the call's options (kernel arguments, so the host keeps no
@@ -219,87 +215,7 @@ __global__ void __launch_bounds__(CTL_THREADS) k_ctl_mixed_after(SolveState *con
   }
 }
 
-// ------------------------------------------------------------ graph building
-struct Builder {
-  cudaGraph_t g = nullptr;
-  std::vector<cudaGraphNode_t> deps;
-  cudaError_t err = cudaSuccess;
-  int kernels = 0;
 
-  explicit Builder(cudaGraph_t graph) : g(graph) {}
-  void kernel(const void *f, dim3 grid, dim3 block, size_t smem, void **args) {
-    if (err != cudaSuccess || grid.x == 0) return;
-    cudaKernelNodeParams kp{};
-    kp.func = const_cast<void *>(f);
-    kp.gridDim = grid;
-    kp.blockDim = block;
-    kp.sharedMemBytes = (unsigned)smem;
-    kp.kernelParams = args;
-    cudaGraphNode_t node;
-    err = cudaGraphAddKernelNode(&node, g, deps.empty() ? nullptr : deps.data(), deps.size(), &kp);
-    if (err == cudaSuccess) { deps.assign(1, node); ++kernels; }
-  }
-  // A WHILE node on `h` after the current dependencies; returns its body graph.
-  cudaGraph_t while_node(cudaGraphConditionalHandle h) {
-    if (err != cudaSuccess) return nullptr;
-    cudaGraphNodeParams cp{};
-    cp.type = cudaGraphNodeTypeConditional;
-    cp.conditional.handle = h;
-    cp.conditional.type = cudaGraphCondTypeWhile;
-    cp.conditional.size = 1;
-    cudaGraphNode_t node;
-    err = cudaGraphAddNode(&node, g, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(), &cp);
-    if (err != cudaSuccess) return nullptr;
-    deps.assign(1, node);
-    return cp.conditional.phGraph_out[0];
-  }
-};
-
-// The persistent loop kernels of every group of L (one launch kind), as nodes.
-void add_groups(Builder &B, const LoopPlan &L, int which, int kind, int use_cond, bool guard_first) {
-  bool guarded = false;
-  for (const PlanGroup &G : L.groups) {
-    if (G.n_units <= 0) continue;
-    const int guard = (guard_first && !guarded) ? 1 : 0;
-    guarded = guarded || guard;
-    KParams p{};
-    p.grids = G.gd_dev;
-    p.units = G.units_dev;
-    p.ls = L.ls;
-    p.kind = kind;
-    p.use_cond = use_cond;
-    p.guard = guard;
-    p.dbg_skip_unit = -1;
-    p.timeout_ns = default_timeout_ns();
-    p.n_units = G.n_units;
-    void *args[] = {&p};
-    if (which == 1)
-      B.kernel(G.ks.k1[kind], dim3(persistent_grid(G.ks, 1, G.n_units)), dim3(G.ks.tb), G.ks.smem1, args);
-    else
-      B.kernel(G.ks.k2[kind], dim3(persistent_grid(G.ks, 2, G.n_units)), dim3(G.ks.tb), G.ks.smem2, args);
-  }
-}
-
-void add_finalize(Builder &B, const LoopPlan &L) {
-  for (const PlanGroup &G : L.groups) {
-    if (G.n_units <= 0) continue;
-    KParams p{};
-    p.grids = G.gd_dev;
-    p.units = G.units_dev;
-    p.ls = L.ls;
-    p.dbg_skip_unit = -1;
-    void *args[] = {&p};
-    B.kernel(G.ks.fin, dim3(G.n_units), dim3(G.ks.tx), 0, args);
-  }
-}
-
-uint64_t loop_budget_ns() {
-  const char *e = getenv("PCG_LOOP_BUDGET_S");
-  const double budget_s = (e && atof(e) > 0) ? atof(e) : 300.0;
-  return (uint64_t)(budget_s * 1e9);
-}
-
-}  // namespace
 
 namespace {
 
