@@ -691,6 +691,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="default workload: skip the batch block")
     ap.add_argument("--no-serve", action="store_true", help="default workload: skip the serving block")
     ap.add_argument("--no-err", action="store_true", help="skip the error against the oracle's tight reference")
+    ap.add_argument("--no-shard", action="store_true", help="default workload: skip the row-band block")
     ap.add_argument("--serve-block-seconds", type=float, default=20.0)
     ap.add_argument("--kernels-only", action="store_true",
                     help="set up the workload and launch each kernel of an iteration 3 times (for ncu)")
@@ -807,6 +808,32 @@ def main():
                  "outer_per_solve": stats_m[-1].outer_iters,
                  "worst_true_relres": max(s.true_relres for s in stats_m), "gpu_launches": int(launches_m),
                  "roofline": _kernel_roofline(pcg, h, b, wl, 1, n_wet, zbar, args.workload, fp64_peak)}
+
+    # the same binary64 solve as row bands of one grid (the multi-GPU layout of
+    # a single large grid, run on this GPU): the cost of the band-edge exchange
+    shard = None
+    if solo and wl["prec"] == 0 and args.workload == DEFAULT_WORKLOAD and not args.no_shard:
+        sh = pcg.Shard(h, 2)
+        row0, halo = sh.bands()
+        for _ in range(args.warmup):
+            sh.solve(b, x, opts)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        steps_s = max(3, args.steps // 2)
+        e0.record(stream)
+        worst_s = 0.0
+        for _ in range(steps_s):
+            sts = sh.solve(b, x, opts)
+            worst_s = max(worst_s, sts.true_relres)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_s = e0.elapsed_time(e1) / steps_s
+        shard = {"bands": 2, "row0": [int(v) for v in row0], "halo_rows": halo, "value": 1e3 / ms_s, "unit": UNIT,
+                 "ms_per_step": ms_s, "steps": steps_s, "iters_per_solve": sts.iters,
+                 "worst_true_relres": worst_s, "vs_whole_grid": (1e3 / ms_s) / value,
+                 "layout": "bands on one GPU: one launch over both bands' units, shared reduction, halo rows "
+                           "copied between band planes after each kernel"}
+        sh.close()
     h.close()
 
     # batching and serving on the same GPU (the metric's "mixed vs FP64" over
@@ -875,6 +902,8 @@ def main():
             line["batch"] = batch
         if serve is not None:
             line["serve"] = serve
+        if shard is not None:
+            line["shard"] = shard
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
