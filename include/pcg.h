@@ -385,14 +385,20 @@ int solver_server_register(pcg_server *s, pcg_handle *h, int32_t *grid_id);
  * device; copied into a device buffer of the grid's pool before this call
  * returns) writing the solution to x_out ([ny][nx], host or device, written
  * when the request completes). If warm_start is nonzero the solve starts from
- * the grid's last solution. done (may be NULL) is called from the scheduler
+ * the grid's last solution: an ocean model solves the free-surface system once
+ * per time step, and the previous step's surface is the natural initial guess
+ * (the paper's x0 of Algorithm 1 is a previous state too), which is why this
+ * argument, absent from a plain queue interface, is part of the call. done (may be NULL) is called from the scheduler
  * thread on completion. A new pool buffer counts against the HBM budget;
  * PCG_EBUDGET if it does not fit (the request is not queued). */
 int solver_server_submit(pcg_server *s, int32_t grid_id, const double *b, double *x_out, int32_t warm_start,
                          void (*done)(void *user, const pcg_stats *stats), void *user, uint64_t *req_id);
 
 /* Wait for one request; fills stats (may be NULL) and returns its status,
- * or PCG_ETIMEOUT if timeout_ms (< 0 = forever) expires first. */
+ * or PCG_ETIMEOUT if timeout_ms (< 0 = forever) expires first. The statistics
+ * (iterations, residuals, latency from submission) are returned here because a
+ * request's caller, not the server, decides what to do with a solve that did
+ * not converge. */
 int solver_server_wait(pcg_server *s, uint64_t req_id, int32_t timeout_ms, pcg_stats *stats);
 
 /* Cancel a request that has not yet been admitted to the device. */
