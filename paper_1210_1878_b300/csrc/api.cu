@@ -46,18 +46,23 @@ static KernelSet pick(int tx, int pattern, int q) {
 static std::mutex g_attr_mu;
 static int prepare_set(KernelSet &k) {
   std::lock_guard<std::mutex> lk(g_attr_mu);
-  for (const void *f : k.k1) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem1));
-  for (const void *f : k.k2) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem2));
+  // every instantiation of each kernel, the claiming ones included (they share
+  // the persistent grid size)
+  std::vector<const void *> f1(k.k1, k.k1 + 4), f2(k.k2, k.k2 + 3);
+  if (k.k1_claim) f1.push_back(k.k1_claim);
+  if (k.k2_claim) f2.push_back(k.k2_claim);
+  for (const void *f : f1) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem1));
+  for (const void *f : f2) CK(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)k.smem2));
   int dev = 0, nsm = 0, b1 = 0, b2 = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   b1 = b2 = 1 << 20;
-  for (const void *f : k.k1) {
+  for (const void *f : f1) {
     int b = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, k.tb, k.smem1));
     b1 = std::min(b1, b);
   }
-  for (const void *f : k.k2) {
+  for (const void *f : f2) {
     int b = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, k.tb, k.smem2));
     b2 = std::min(b2, b);
@@ -261,11 +266,12 @@ static int launch(const void *f, int grid, int block, size_t smem, KParams p, cu
   return PCG_OK;
 }
 
-// Kernel 1 (which = 1) or 2 over n_units units, persistent CTAs.
-static int launch_k(const KernelSet &ks, int which, int n_units, KParams p, cudaStream_t s) {
+// Kernel 1 (which = 1) or 2 over n_units units, persistent CTAs (claiming
+// units where `dynamic` and the set has a claiming instantiation of the kind).
+static int launch_k(const KernelSet &ks, int which, int n_units, KParams p, cudaStream_t s, bool dynamic = false) {
   p.n_units = n_units;
   if (p.kind < 0 || p.kind >= (which == 1 ? 4 : 3)) { set_error("invalid launch kind"); return PCG_EINVAL; }
-  return launch(which == 1 ? ks.k1[p.kind] : ks.k2[p.kind], persistent_grid(ks, which, n_units), ks.tb,
+  return launch(loop_kernel(ks, which, p.kind, dynamic), persistent_grid(ks, which, n_units), ks.tb,
                 which == 1 ? ks.smem1 : ks.smem2, p, s);
 }
 
@@ -301,7 +307,8 @@ static int build_loop_graph(LoopPlan &L) {
       params.back().n_units = G.n_units;
       void *args[] = {&params.back()};
       cudaKernelNodeParams kp{};
-      kp.func = const_cast<void *>(pass == 0 ? G.ks.k1[K1_ITER] : G.ks.k2[K2_ITER]);
+      kp.func = const_cast<void *>(loop_kernel(G.ks, pass == 0 ? 1 : 2, pass == 0 ? (int)K1_ITER : (int)K2_ITER,
+                                               L.dynamic));
       kp.gridDim = dim3(persistent_grid(G.ks, pass == 0 ? 1 : 2, G.n_units));
       kp.blockDim = dim3(G.ks.tb);
       kp.sharedMemBytes = (unsigned)(pass == 0 ? G.ks.smem1 : G.ks.smem2);
@@ -334,6 +341,8 @@ int members_arm(LoopPlan &L, LaunchState *ls_host, int active, int max_launches,
   ls_host->t0_ns = 0;
   ls_host->timed_out = 0;
   ls_host->cond_cleared = 0;
+  ls_host->claim_next = 0;
+  ls_host->claim_exit = 0;
   const char *e = getenv("PCG_LOOP_BUDGET_S");
   const double budget_s = (e && atof(e) > 0) ? atof(e) : 300.0;
   ls_host->budget_ns = (uint64_t)(budget_s * 1e9);
@@ -361,7 +370,7 @@ int members_loop(LoopPlan &L, LaunchState *ls_host, int max_launches, cudaStream
           const int guard = (pass == 1 && !guarded) ? 1 : 0;
           guarded = guarded || guard;
           int rc = launch_k(G.ks, pass == 0 ? 1 : 2, G.n_units,
-                            kparams(L, G, pass == 0 ? (int)K1_ITER : (int)K2_ITER, 0, guard), s);
+                            kparams(L, G, pass == 0 ? (int)K1_ITER : (int)K2_ITER, 0, guard), s, L.dynamic);
           if (rc) return rc;
         }
     }
@@ -435,6 +444,11 @@ static int plan_build_t(LoopPlan &L, pcg_handle *const *hs, int n, bool with_gra
                         DevPlanes<T> pcg_handle::*planes, cudaStream_t s) {
   if (n > INT16_MAX) { set_error("more than 32767 grids in one plan"); return PCG_EINVAL; }   // 16-bit grid index
   L.ls = ls;
+  // Claiming pays where the units finish unevenly: the grids of a batch differ
+  // in size and retire at different iterations. The binary64 kernels keep the
+  // fixed stride, which gives each SM's FP64 pipe an equal share (their sets
+  // have no claiming instantiation).
+  L.dynamic = n > 1;
   std::vector<std::vector<int>> groups;
   for (int i = 0; i < n; ++i) {
     bool placed = false;

@@ -73,6 +73,8 @@ struct LaunchState {
   int32_t cond_cleared;    // the loop condition has been cleared in this launch
   int32_t bodies_total;    // loop-body executions over every pass of a solve (launch count)
   int32_t passes;          // outer passes of a solve (restarts / refinement steps + 1)
+  uint32_t claim_next;     // next unit of a running claiming launch (0 between launches)
+  uint32_t claim_exit;     // CTAs of the running claiming launch that have finished (0 between launches)
 };
 
 // A CUtensorMap as the kernels see it: 128 opaque bytes, 64-byte aligned.

@@ -24,7 +24,8 @@ namespace pcg {
   } while (0)
 
 struct KernelSet {
-  const void *k1[4] = {}, *k2[3] = {};      // per launch kind (K1_*, K2_*)
+  const void *k1[4] = {}, *k2[3] = {};      // per launch kind (K1_*, K2_*), fixed stride
+  const void *k1_claim = nullptr, *k2_claim = nullptr;   // K1_ITER / K2_ITER claiming units (binary32 only)
   const void *fin = nullptr, *pack = nullptr, *unpack = nullptr;
   size_t smem1 = 0, smem2 = 0;
   int tx = 0;        // strip width: threads of the small kernels
@@ -34,6 +35,13 @@ struct KernelSet {
   int ctas1 = 0, ctas2 = 0;                   // resident CTAs on the device (persistent grid size)
   bool ok = false;
 };
+
+// The kernel of a loop launch: the claiming instantiation of an iteration
+// kind where the plan claims and the set has one, else the fixed stride.
+inline const void *loop_kernel(const KernelSet &ks, int which, int kind, bool dynamic) {
+  if (which == 1) return (dynamic && kind == K1_ITER && ks.k1_claim) ? ks.k1_claim : ks.k1[kind];
+  return (dynamic && kind == K2_ITER && ks.k2_claim) ? ks.k2_claim : ks.k2[kind];
+}
 
 // Strips whose preconditioner t phase (TX + 2R columns) fills whole warps:
 // 64 - 2R columns for binary64, 124 for binary32 (a multiple of 4, for the
@@ -145,6 +153,7 @@ struct LoopPlan {
   cudaGraphConditionalHandle cond = 0;
   bool graph_ok = false;
   int body_kernels = 0;            // kernel nodes in the loop body
+  bool dynamic = false;            // iteration kernels claim units one at a time, where their set can
   std::vector<void *> owned;       // device allocations of a batch plan
   std::unique_ptr<SolveGraph> solve;   // whole-solve graph of a handle alone (built on first use)
   bool solve_tried = false;            // its construction was attempted (and may have failed)

@@ -10,13 +10,17 @@ namespace pcg {
 template <typename T, int TX, class P>
 KernelSet make_set() {
   KernelSet k;
-  k.k1[K1_ITER] = (const void *)k_stencil<T, TX, K1_ITER>;
-  k.k1[K1_RESID_INIT] = (const void *)k_stencil<T, TX, K1_RESID_INIT>;
-  k.k1[K1_RESID_CHECK] = (const void *)k_stencil<T, TX, K1_RESID_CHECK>;
-  k.k1[K1_SPMV] = (const void *)k_stencil<T, TX, K1_SPMV>;
-  k.k2[K2_ITER] = (const void *)k_precond<T, TX, P, K2_ITER>;
-  k.k2[K2_INIT] = (const void *)k_precond<T, TX, P, K2_INIT>;
-  k.k2[K2_APPLY] = (const void *)k_precond<T, TX, P, K2_APPLY>;
+  k.k1[K1_ITER] = (const void *)k_stencil<T, TX, K1_ITER, false>;
+  k.k1[K1_RESID_INIT] = (const void *)k_stencil<T, TX, K1_RESID_INIT, false>;
+  k.k1[K1_RESID_CHECK] = (const void *)k_stencil<T, TX, K1_RESID_CHECK, false>;
+  k.k1[K1_SPMV] = (const void *)k_stencil<T, TX, K1_SPMV, false>;
+  k.k2[K2_ITER] = (const void *)k_precond<T, TX, P, K2_ITER, false>;
+  k.k2[K2_INIT] = (const void *)k_precond<T, TX, P, K2_INIT, false>;
+  k.k2[K2_APPLY] = (const void *)k_precond<T, TX, P, K2_APPLY, false>;
+  if constexpr (sizeof(T) == 4) {   // batches' binary32 inner iterations claim units
+    k.k1_claim = (const void *)k_stencil<T, TX, K1_ITER, true>;
+    k.k2_claim = (const void *)k_precond<T, TX, P, K2_ITER, true>;
+  }
   k.fin = (const void *)k_finalize<T, TX>;
   k.pack = (const void *)k_pack<T, double, TX>;
   k.unpack = (const void *)k_unpack<T, double>;

@@ -282,7 +282,16 @@ __device__ __forceinline__ void flag_timeout(SolveState *st) { atomicCAS(&st->st
 // ------------------------------------------------------------ row-group streaming
 // A CTA is TX compute threads plus one producer warp, and it is persistent:
 // it takes the units blockIdx.x, blockIdx.x + gridDim.x, ... of the launch's
-// list. The producer streams the input fields of its units, unit after unit
+// list (the fixed stride; CTAs are placed round robin on the SMs, so every SM
+// gets the same share of equal units, which is what the binary64 kernels,
+// bound by each SM's FP64 pipe, need). The claiming instantiations (DYN)
+// instead take one unit at a time from a counter in the launch state, so that
+// a CTA that finishes early takes more: a batch's units come from grids of
+// different sizes that retire at different iterations. Their producer warp
+// claims and hands each unit to the compute threads through a small queue in
+// shared memory. Which CTA runs a unit does not change its result: partial
+// sums are kept per unit and added in unit order.
+// The producer streams the input fields of its units, unit after unit
 // without a pause, in groups of RB consecutive rows into a ring of NSG group
 // slots. Lane f of the producer owns field f and issues one copy per group: a
 // 2D tensor tile of RB rows (cp.async.bulk.tensor) when RB > 1, a 1D bulk copy
@@ -294,8 +303,10 @@ __device__ __forceinline__ void flag_timeout(SolveState *st) { atomicCAS(&st->st
 // here (each occupies its issuing thread for a few hundred ns on this GPU), so
 // several rows per copy is what lets a few CTAs per SM keep HBM busy.
 
-// control words at the start of shared memory (after the barriers)
-enum { CTL_ABORT = 0, CTL_ARMED = 1, CTL_SEEN = 2, CTL_FLAG = 3 };
+// control words at the start of shared memory (after the barriers); the
+// claiming kernels' unit queue (UQ entries) fills the rest of the 64 bytes
+enum { CTL_ABORT = 0, CTL_ARMED = 1, CTL_SEEN = 2, CTL_FLAG = 3, CTL_PUB = 4, CTL_CONS = 5, CTL_CUR = 6, CTL_QUEUE = 8 };
+constexpr int UQ = 8;
 
 struct FieldCopy {
   const char *src;      // RB = 1: element (first box column, row 0) of the plane, as bytes
@@ -363,22 +374,74 @@ __device__ __forceinline__ int skip_grid(int ui, int u_end) {
   return u_end <= ui ? ui + g : ui + (u_end - ui + g - 1) / g * g;
 }
 
+// Wait until pred() holds, giving up after timeout_ns (one thread).
+template <class Pred>
+__device__ __forceinline__ bool spin_bounded(Pred pred, uint64_t timeout_ns) {
+  if (pred()) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (pred()) return true;
+    if ((it & 63u) == 0 && global_ns() - t0 > timeout_ns) return false;
+  }
+}
+
+// Claiming: the launch's next unit (lane 0 takes it, the warp shares it).
+__device__ __forceinline__ int claim_unit(const KParams &p, int lane) {
+  int ui = 0;
+  if (lane == 0) ui = (int)atomicAdd(&p.ls->claim_next, 1u);
+  return __shfl_sync(0xffffffffu, ui, 0);
+}
+
+// Claiming: append unit v (-1: no more) to the unit queue once there is room,
+// as the producer's pub-th entry. False if the compute threads took no entry
+// for timeout_ns (the CTA is then marked aborting).
+__device__ __forceinline__ bool queue_push(volatile int *ctl, int pub, int v, int lane, uint64_t timeout_ns) {
+  bool ok = true;
+  if (lane == 0) {
+    ok = spin_bounded([&] { return pub - ctl[CTL_CONS] < UQ; }, timeout_ns);
+    if (ok) {
+      ctl[CTL_QUEUE + pub % UQ] = v;
+      __threadfence_block();
+      ctl[CTL_PUB] = pub + 1;
+    } else {
+      ctl[CTL_ABORT] = 1;
+    }
+  }
+  return __shfl_sync(0xffffffffu, ok, 0);
+}
+
 // The producer warp's loop: lane f issues the copies of field f of every
 // group of the CTA's units, in order. setup(ui, f, c, has, mlo, ng, u_end)
 // describes unit ui's field f (returns false when ui's grid is to be skipped,
 // with u_end the end of that grid's units). Returns the number of groups
-// armed; stops early once the CTA is aborting.
-template <int NSG, int RB, class Setup>
+// armed. With the fixed stride the compute threads walk the same units and
+// take the same skip decisions themselves, and the producer stops early once
+// the CTA is aborting. With DYN a skipped grid's remaining units are passed
+// over by raising the claim counter past them, every other unit is queued for
+// the compute threads before its copies are issued, units are still queued
+// (without copies) once the CTA is aborting, so that the compute threads join
+// every unit's reduction, and -1 ends the queue.
+template <int NSG, int RB, bool DYN, class Setup>
 __device__ __forceinline__ uint32_t produce_all(const KParams &p, unsigned char *ring, int group_bytes, uint64_t *full,
                                                 uint64_t *empty, volatile int *ctl, Setup setup) {
   const int lane = threadIdx.x & 31;
   uint32_t gq = 0;
   int last_g = -1;
-  for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
+  int pub = 0;             // DYN: units queued
+  bool stopped = false;    // DYN: no more copies, the CTA is aborting
+  for (int ui = DYN ? claim_unit(p, lane) : (int)blockIdx.x; ui < p.n_units;
+       ui = DYN ? claim_unit(p, lane) : ui + (int)gridDim.x) {
     FieldCopy c{};
     bool has = false;
     int mlo = 0, ng = 0, u_end = 0;
-    if (!setup(ui, lane, c, has, mlo, ng, u_end)) {
+    if constexpr (DYN) {
+      if (!__shfl_sync(0xffffffffu, setup(ui, lane, c, has, mlo, ng, u_end), 0)) {
+        if (lane == 0 && u_end > ui + 1) atomicMax(&p.ls->claim_next, (unsigned)u_end);
+        continue;
+      }
+      if (!queue_push(ctl, pub++, ui, lane, p.timeout_ns)) return gq;
+      if (stopped) continue;
+    } else if (!setup(ui, lane, c, has, mlo, ng, u_end)) {
       ui = skip_grid(ui, u_end) - (int)gridDim.x;
       continue;
     }
@@ -395,7 +458,9 @@ __device__ __forceinline__ uint32_t produce_all(const KParams &p, unsigned char 
         if (lane == 0) ok = mbar_wait_or_abort(&empty[slot], (fill - 1) & 1u, p.timeout_ns, &ctl[CTL_ABORT]);
         if (!__shfl_sync(0xffffffffu, ok, 0)) {
           if (lane == 0) ctl[CTL_ABORT] = 1;
-          return gq;
+          if constexpr (!DYN) return gq;
+          stopped = true;
+          break;
         }
       }
       if (lane == 0) mbar_arrive_expect_tx(&full[slot], total);
@@ -409,7 +474,44 @@ __device__ __forceinline__ uint32_t produce_all(const KParams &p, unsigned char 
       }
     }
   }
+  if constexpr (DYN) queue_push(ctl, pub, -1, lane, p.timeout_ns);
   return gq;
+}
+
+// The compute threads' first unit (k = 0) and the ones after unit ui (k-th):
+// the fixed stride, or with DYN the producer's k-th queue entry, which thread
+// 0 waits for (bounded) and shares through ctl[CTL_CUR]. -1: no more units.
+template <bool DYN, int NC>
+__device__ __forceinline__ int compute_unit(const KParams &p, volatile int *ctl, int k, int ui) {
+  if constexpr (!DYN) {
+    ui = k == 0 ? (int)blockIdx.x : ui + (int)gridDim.x;
+    return ui < p.n_units ? ui : -1;
+  } else {
+    if (threadIdx.x == 0) {
+      const bool ok = spin_bounded([&] { return ctl[CTL_PUB] > k; }, p.timeout_ns);
+      __threadfence_block();
+      ctl[CTL_CUR] = ok ? ctl[CTL_QUEUE + k % UQ] : -1;
+      if (!ok) ctl[CTL_ABORT] = 1;
+    }
+    compute_sync<NC>();
+    ui = ctl[CTL_CUR];
+    compute_sync<NC>();
+    if (threadIdx.x == 0) ctl[CTL_CONS] = k + 1;
+    return ui;
+  }
+}
+
+// End of a claiming launch: the last CTA to leave resets the claim counters
+// for the next launch (every CTA has finished claiming by then).
+__device__ __forceinline__ void launch_exit(LaunchState *ls) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&ls->claim_exit, 1u) + 1u == gridDim.x) {
+      ls->claim_next = 0u;
+      ls->claim_exit = 0u;
+      __threadfence();
+    }
+  }
 }
 
 // Shared-memory geometry common to both kernels: barriers and control words
@@ -730,7 +832,7 @@ struct K1Unit {
   }
 };
 
-template <typename T, int TX, int KIND>
+template <typename T, int TX, int KIND, bool DYN>
 __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
   using G = K1Geom<T, TX>;
   extern __shared__ unsigned char smem_raw[];
@@ -745,6 +847,7 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
   if (tid == 0) {
     for (int s = 0; s < G::NSG; ++s) { mbar_init(&rc.full[s], 1); mbar_init(&rc.empty[s], 1); }
     rc.ctl[CTL_ABORT] = 0; rc.ctl[CTL_ARMED] = 0; rc.ctl[CTL_SEEN] = 0; rc.ctl[CTL_FLAG] = 0;
+    rc.ctl[CTL_PUB] = 0; rc.ctl[CTL_CONS] = 0;
     fence_mbar_init();
   }
   __syncthreads();
@@ -792,19 +895,22 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
       return true;
     };
     const uint32_t gq =
-        produce_all<G::NSG, G::RB>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, setup);
+        produce_all<G::NSG, G::RB, DYN>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, setup);
     if (tid == G::NC) rc.ctl[CTL_ARMED] = (int)gq;
   } else {
     // ---- compute threads
     uint32_t gbase = 0, seen = 0;
     bool aborted = false;
-    for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
+    for (int k = 0, ui = compute_unit<DYN, G::NC>(p, rc.ctl, 0, 0); ui >= 0;
+         ui = compute_unit<DYN, G::NC>(p, rc.ctl, ++k, ui)) {
       const Unit un = p.units[ui];
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
       SolveState *st = gdp->st;
-      if (skip_unit(st)) {
-        ui = skip_grid(ui, gdp->u_off + gdp->n_units) - (int)gridDim.x;
-        continue;
+      if constexpr (!DYN) {                  // (claimed units of skipped grids are never queued)
+        if (skip_unit(st)) {
+          ui = skip_grid(ui, gdp->u_off + gdp->n_units) - (int)gridDim.x;
+          continue;
+        }
       }
       const int nx = gdp->nx, ny = gdp->ny;
       const int i0 = un.sx * TX, j0 = gdp->own0 + un.sy * gdp->ty;
@@ -860,6 +966,7 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
   }
   __syncthreads();
   drain_groups<G::NSG>(rc, p.timeout_ns);
+  if constexpr (DYN) launch_exit(ls);
 }
 
 // ------------------------------------------------------------ kernel 2
@@ -1083,7 +1190,7 @@ struct K2Unit {
   }
 };
 
-template <typename T, int TX, class P, int KIND>
+template <typename T, int TX, class P, int KIND, bool DYN>
 __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
   using G = K2Geom<T, TX, P>;
   constexpr int R = P::R, LD = P::LD, NZ = P::NZ, NW = P::NW;
@@ -1101,6 +1208,7 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
   if (tid == 0) {
     for (int s = 0; s < G::NSG; ++s) { mbar_init(&rc.full[s], 1); mbar_init(&rc.empty[s], 1); }
     rc.ctl[CTL_ABORT] = 0; rc.ctl[CTL_ARMED] = 0; rc.ctl[CTL_SEEN] = 0; rc.ctl[CTL_FLAG] = 0;
+    rc.ctl[CTL_PUB] = 0; rc.ctl[CTL_CONS] = 0;
     fence_mbar_init();
   }
   __syncthreads();
@@ -1140,19 +1248,22 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
       return true;
     };
     const uint32_t gq =
-        produce_all<G::NSG, G::RB>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, setup);
+        produce_all<G::NSG, G::RB, DYN>(p, rc.ring, G::GROUP, rc.full, rc.empty, rc.ctl, setup);
     if (tid == G::NC) rc.ctl[CTL_ARMED] = (int)gq;
   } else {
     // ---- compute threads
     uint32_t gbase = 0, seen = 0;
     bool aborted = false;
-    for (int ui = blockIdx.x; ui < p.n_units; ui += gridDim.x) {
+    for (int k = 0, ui = compute_unit<DYN, G::NC>(p, rc.ctl, 0, 0); ui >= 0;
+         ui = compute_unit<DYN, G::NC>(p, rc.ctl, ++k, ui)) {
       const Unit un = p.units[ui];
       const GridDev<T> *gdp = reinterpret_cast<const GridDev<T> *>(p.grids) + un.g;
       SolveState *st = gdp->st;
-      if (skip_unit(st)) {
-        ui = skip_grid(ui, gdp->u_off + gdp->n_units) - (int)gridDim.x;
-        continue;
+      if constexpr (!DYN) {                  // (claimed units of skipped grids are never queued)
+        if (skip_unit(st)) {
+          ui = skip_grid(ui, gdp->u_off + gdp->n_units) - (int)gridDim.x;
+          continue;
+        }
       }
       const int nx = gdp->nx, ny = gdp->ny;
       const int i0 = un.sx * TX, j0 = gdp->own0 + un.sy * gdp->ty;
@@ -1210,6 +1321,7 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
   }
   __syncthreads();
   drain_groups<G::NSG>(rc, p.timeout_ns);
+  if constexpr (DYN) launch_exit(ls);
 }
 
 // ------------------------------------------------------------ small kernels

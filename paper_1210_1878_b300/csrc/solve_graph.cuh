@@ -76,9 +76,11 @@ inline void add_groups(Builder &B, const LoopPlan &L, int which, int kind, int u
     p.n_units = G.n_units;
     void *args[] = {&p};
     if (which == 1)
-      B.kernel(G.ks.k1[kind], dim3(persistent_grid(G.ks, 1, G.n_units)), dim3(G.ks.tb), G.ks.smem1, args);
+      B.kernel(loop_kernel(G.ks, 1, kind, L.dynamic), dim3(persistent_grid(G.ks, 1, G.n_units)), dim3(G.ks.tb),
+               G.ks.smem1, args);
     else
-      B.kernel(G.ks.k2[kind], dim3(persistent_grid(G.ks, 2, G.n_units)), dim3(G.ks.tb), G.ks.smem2, args);
+      B.kernel(loop_kernel(G.ks, 2, kind, L.dynamic), dim3(persistent_grid(G.ks, 2, G.n_units)), dim3(G.ks.tb),
+               G.ks.smem2, args);
   }
 }
 
