@@ -684,7 +684,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="binary64 workloads: skip the mixed-precision companion")
@@ -780,7 +780,8 @@ def main():
     value = replicated_rate(args.steps, ms, world)
     worst_true = max(s.true_relres for s in stats)
 
-    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
+    # end to end through the C ABI with pinned host buffers (copies inside the timed region):
+    # one handle, each solve waited for before the next
     bh = torch.from_numpy(grid.b.copy()).pin_memory()
     xh = torch.zeros_like(bh).pin_memory()
     pcg.pcg_solve(h, bh, xh, opts)
@@ -792,7 +793,33 @@ def main():
         pcg.pcg_solve(h, bh, xh, opts)
     e3.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = max_over_ranks(e2.elapsed_time(e3))
+    ms_e2e_serial = max_over_ranks(e2.elapsed_time(e3))
+    # and pipelined: two handles of the grid (pcg_clone), solves alternating
+    # between them, each synchronised only before its handle is used again, so
+    # that one solve's host copies (on its handle's copy stream) overlap the
+    # other's iterations
+    h2 = pcg.pcg_clone(h)
+    bh2 = torch.from_numpy(grid.b.copy()).pin_memory()
+    xh2 = torch.zeros_like(bh2).pin_memory()
+    pcg.pcg_solve(h2, bh2, xh2, opts)
+    pipe = [(h, bh, xh), (h2, bh2, xh2)]
+    pipe_stats = []
+    torch.cuda.synchronize()
+    e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e4.record(stream)
+    for k in range(args.e2e_steps):
+        hh, bb, xx = pipe[k % 2]
+        pipe_stats.append(pcg.pcg_solve(hh, bb, xx, opts, sync=False))
+    pipe_rc = [pcg.pcg_sync(hh) for hh, _, _ in pipe]
+    e5.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(e4.elapsed_time(e5))
+    if any(rc != pcg.PCG_OK for rc in pipe_rc) or any(s.status != pcg.PCG_OK for s in pipe_stats):
+        raise RuntimeError("pipelined end-to-end solves did not converge")
+    if not (np.array_equal(xh.numpy(), xh2.numpy()) and np.array_equal(xh.numpy(), x_main)):
+        raise RuntimeError("pipelined end-to-end solutions differ from the device-timed solve")
+    h2.close()
     e2e_value = replicated_rate(args.e2e_steps, ms_e2e, world)
     vec_bytes = grid.nx * grid.ny * 8
 
@@ -893,7 +920,12 @@ def main():
                        "l2": _l2_label(torch, n_wet * (4 if wl["prec"] == 1 else 8) * (14 + zbar)),
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": vec_bytes,
-                    "d2h_bytes_per_step": vec_bytes},
+                    "d2h_bytes_per_step": vec_bytes, "steps": args.e2e_steps,
+                    "pipeline": "two handles of the grid (pcg_clone), pinned host b and x, solves alternating and "
+                                "each synchronised before its handle is reused: one solve's host copies overlap "
+                                "the other's iterations",
+                    "serial": {"value": replicated_rate(args.e2e_steps, ms_e2e_serial, world), "unit": UNIT,
+                               "note": "one handle, each solve synchronised before the next"}},
             "gpu_launches": int(launches),
             "clocks": clocks,
             "roofline": roof,

@@ -157,12 +157,17 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
  * pcg_sync(h), which returns the solve's status: PCG_OK, PCG_ENOTCONV (x holds
  * the last iterate), PCG_EBREAKDOWN, PCG_ETIMEOUT. This call returns PCG_OK once
  * the solve is enqueued, or an error found before (PCG_EINVAL, PCG_ENOMEM,
- * PCG_ECUDA). b may be reused as soon as the call returns.
+ * PCG_ECUDA).
  * One solve may be in flight per handle: a call on a handle whose previous
  * solve has not been synchronised first waits for it (as pcg_sync does), and so
- * do the other entry points that use the handle. Host buffers: b is staged
- * at the call; a pageable host x makes the call wait for the solve (the copy
- * into pageable memory completes synchronously), a pinned one does not.
+ * do the other entry points that use the handle. Host buffers go through the
+ * handle's device staging buffer, copied on the handle's own copy stream and
+ * ordered against cuda_stream by events, so that they overlap other work on
+ * cuda_stream (another handle's solve; see pcg_clone). A device or pageable
+ * host b may be reused as soon as the call returns (a pageable one is staged
+ * at the call); a pinned host b must stay unchanged until pcg_sync(h). A
+ * pageable host x makes the call wait for the solve (the copy into pageable
+ * memory completes synchronously), a pinned one does not.
  * Without conditional CUDA graphs (or with PCG_LOOP_CHUNKED set) the solve is
  * done by a host-driven loop before the call returns; pcg_sync then only
  * reports it. */
@@ -181,11 +186,23 @@ int pcg_solve(pcg_handle *h, const double *b, double *x, const pcg_opts *opts, p
 int pcg_solve_batched(pcg_handle *const *hs, int32_t nbatch, const double *const *b, double *const *x,
                       const pcg_opts *opts, pcg_stats *stats, void *cuda_stream);
 
-/* Wait for the solve enqueued on h (pcg_solve or pcg_solve_batched), fill its
- * statistics and return its status (see pcg_solve_batched for a batch). With
- * nothing in flight, returns the status of h's last synchronised solve
- * (PCG_OK if none). PCG_ECUDA if the stream reported an error. */
+/* Wait for the solve enqueued on h (pcg_solve or pcg_solve_batched): its work
+ * on its stream, not what was queued there after it, and the copies of its
+ * solutions into host buffers. Fill its statistics and return its status (see
+ * pcg_solve_batched for a batch). With nothing in flight, returns the status of
+ * h's last synchronised solve (PCG_OK if none). PCG_ECUDA if the device
+ * reported an error. */
 int pcg_sync(pcg_handle *h);
+
+/* A second handle of the same grid and factor: a copy of src's host grid, Z
+ * and D, and strips, with device planes, state and staging of its own (no
+ * factorisation). Since one solve may be in flight per handle, two handles of
+ * one grid let a caller keep two solves in flight, e.g. alternate right-hand
+ * sides between them so that one solve's host copies overlap the other's
+ * iterations. The paper has no counterpart. src is only read (it may have a
+ * solve in flight). Errors: PCG_EINVAL (null pointers), PCG_ENOMEM, PCG_ECUDA.
+ * Free the copy with pcg_free. */
+int pcg_clone(const pcg_handle *src, void *cuda_stream, pcg_handle **out);
 
 /* q = A v on the device kernels of the iteration (Section 3, Eq. 9).
  * Returns PCG_OK, PCG_EINVAL, PCG_ECUDA, or PCG_ETIMEOUT when a bounded device

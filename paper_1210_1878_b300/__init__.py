@@ -25,7 +25,7 @@ PCG_PAT_TRIL_A, PCG_PAT_TRIL_A2, PCG_PAT_FULL, PCG_PAT_BAND_T, PCG_PAT_DIAG = ra
 PCG_FP64, PCG_MIXED = 0, 1
 
 EXPORTED = [
-    "ainv_setup", "ainv_factor_host", "pcg_solve", "pcg_solve_batched", "pcg_sync", "pcg_spmv", "pcg_spmv_noalloc", "pcg_precond_apply",
+    "ainv_setup", "ainv_factor_host", "pcg_clone", "pcg_solve", "pcg_solve_batched", "pcg_sync", "pcg_spmv", "pcg_spmv_noalloc", "pcg_precond_apply",
     "pcg_apply_f32", "pcg_autotune", "pcg_tiles",
     "pcg_ainv_export", "pcg_resident_bytes", "pcg_n_wet", "pcg_free", "pcg_status_string",
     "pcg_last_error_message", "pcg_debug_wait_timeout", "pcg_profile_kernels", "pcg_kernel_launches",
@@ -100,6 +100,7 @@ def _load():
         "pcg_resident_bytes": (C.c_size_t, [vp]),
         "pcg_n_wet": (i32, [vp]),
         "pcg_free": (None, [vp]),
+        "pcg_clone": (C.c_int, [vp, vp, C.POINTER(vp)]),
         "pcg_status_string": (C.c_char_p, [C.c_int]),
         "pcg_last_error_message": (C.c_char_p, []),
         "pcg_debug_wait_timeout": (C.c_int, [vp, i32, dbl, vp]),
@@ -218,6 +219,16 @@ def ainv_setup(nx, ny, wet, c_e, c_n, shift, pattern=PCG_PAT_TRIL_A2, drop_tol=0
 
 def ainv_setup_grid(grid, **kw) -> Handle:
     return ainv_setup(grid.nx, grid.ny, grid.wet, grid.c_e, grid.c_n, grid.shift, **kw)
+
+
+def pcg_clone(h: Handle, stream=None) -> Handle:
+    """A second handle of h's grid and factor (pcg_clone): its own device
+    planes, so that two solves of the grid can be in flight."""
+    out = C.c_void_p()
+    st = lib.pcg_clone(h.ptr, _stream(stream), C.byref(out))
+    if st != PCG_OK:
+        raise PCGError(st, "pcg_clone")
+    return Handle(out.value, h.nx, h.ny)
 
 
 def ainv_factor_host(nx, ny, wet, c_e, c_n, shift, pattern=PCG_PAT_TRIL_A2, drop_tol=0.0, band_q=0):

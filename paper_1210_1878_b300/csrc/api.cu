@@ -389,34 +389,64 @@ bool is_device_ptr(const void *p) {
 }
 
 // Pack a user [ny][nx] binary64 vector into plane `which` (0 b, 1 x, 2 r0, 3 d0).
+// A host `user` vector goes through h->stage: copied on s, or with
+// `on_copy_stream` on the handle's copy stream (s then waits for the copy).
+// Either way the copy waits for the previous use of stage.
 template <typename T>
-static int pack_user(pcg_handle *h, DevPlanes<T> &P, const double *user, int which, cudaStream_t s) {
+static int pack_user(pcg_handle *h, DevPlanes<T> &P, const double *user, int which, cudaStream_t s,
+                     bool on_copy_stream = false) {
   const double *srcp = user;
-  if (!is_device_ptr(user)) {
-    CK(cudaMemcpyAsync(h->stage, user, sizeof(double) * (size_t)P.nx * P.ny, cudaMemcpyHostToDevice, s));
+  const bool host = !is_device_ptr(user);
+  if (host) {
+    const size_t bytes = sizeof(double) * (size_t)P.nx * P.ny;
+    if (on_copy_stream) {
+      CK(cudaStreamWaitEvent(h->copy_stream, h->ev_stage, 0));
+      CK(cudaMemcpyAsync(h->stage, user, bytes, cudaMemcpyHostToDevice, h->copy_stream));
+      CK(cudaEventRecord(h->ev_in, h->copy_stream));
+      CK(cudaStreamWaitEvent(s, h->ev_in, 0));
+    } else {
+      CK(cudaStreamWaitEvent(s, h->ev_stage, 0));
+      CK(cudaMemcpyAsync(h->stage, user, bytes, cudaMemcpyHostToDevice, s));
+    }
     srcp = h->stage;
   }
   KParams p{};
   p.grids = P.gd_dev; p.units = P.units_dev;
-  if (P.n_units == 0) return PCG_OK;
-  void *args[] = {&p, (void *)&srcp, &which};
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  CK(cudaLaunchKernel(P.ks.pack, dim3(P.n_units), dim3(P.tx), args, 0, s));
+  if (P.n_units > 0) {
+    void *args[] = {&p, (void *)&srcp, &which};
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    CK(cudaLaunchKernel(P.ks.pack, dim3(P.n_units), dim3(P.tx), args, 0, s));
+  }
+  if (host) CK(cudaEventRecord(h->ev_stage, s));   // stage is free once the pack has read it
   return PCG_OK;
 }
 
 // Unpack plane `which` (0 x, 1 s, 2 q) into a user [ny][nx] binary64 vector.
+// A host `user` vector goes through h->stage (after its previous use), copied
+// back on s, or with `on_copy_stream` on the handle's copy stream.
 template <typename T>
-static int unpack_user(pcg_handle *h, DevPlanes<T> &P, double *user, int which, cudaStream_t s) {
+static int unpack_user(pcg_handle *h, DevPlanes<T> &P, double *user, int which, cudaStream_t s,
+                       bool on_copy_stream = false) {
   const bool dev = is_device_ptr(user);
   double *dst = dev ? user : h->stage;
+  if (!dev) CK(cudaStreamWaitEvent(s, h->ev_stage, 0));
   const GridDev<T> *gdp = P.gd_dev;
   void *args[] = {(void *)&gdp, (void *)&dst, &which};
   const size_t n = (size_t)P.nx * P.ny;
   const int blocks = (int)std::min<size_t>((n + 255) / 256, 148 * 16);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   CK(cudaLaunchKernel(P.ks.unpack, dim3(std::max(blocks, 1)), dim3(256), args, 0, s));
-  if (!dev) CK(cudaMemcpyAsync(user, h->stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  if (!dev) {
+    if (on_copy_stream) {
+      CK(cudaEventRecord(h->ev_unpacked, s));
+      CK(cudaStreamWaitEvent(h->copy_stream, h->ev_unpacked, 0));
+      CK(cudaMemcpyAsync(user, h->stage, sizeof(double) * n, cudaMemcpyDeviceToHost, h->copy_stream));
+      CK(cudaEventRecord(h->ev_stage, h->copy_stream));
+    } else {
+      CK(cudaMemcpyAsync(user, h->stage, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+      CK(cudaEventRecord(h->ev_stage, s));
+    }
+  }
   return PCG_OK;
 }
 
@@ -535,9 +565,9 @@ void fill_opts(const pcg_opts *o, pcg_opts &out) {
 static int member_inputs(Member &m, const pcg_opts &o, bool pack_x0, cudaStream_t s) {
   auto &P = m.h->p64;
   int rc;
-  if ((rc = pack_user(m.h, m.h->p64, m.b, 0, s))) return rc;
+  if ((rc = pack_user(m.h, m.h->p64, m.b, 0, s, true))) return rc;
   if (o.use_x0) {
-    if (pack_x0 && (rc = pack_user(m.h, m.h->p64, m.x, 1, s))) return rc;
+    if (pack_x0 && (rc = pack_user(m.h, m.h->p64, m.x, 1, s, true))) return rc;
   } else {
     CK(cudaMemsetAsync(P.plane_start(P.vec(0)), 0, P.plane_elems * sizeof(double), s));
   }
@@ -614,7 +644,7 @@ bool member_decide(Member &m, const pcg_opts &o, bool overrun, cudaStream_t s, i
   return true;
 }
 
-int member_store(Member &m, cudaStream_t s) { return unpack_user(m.h, m.h->p64, m.x, 0, s); }
+int member_store(Member &m, cudaStream_t s) { return unpack_user(m.h, m.h->p64, m.x, 0, s, true); }
 
 void member_stats(Member &m) {
   SolveState &st = *m.st_host;
@@ -1060,6 +1090,36 @@ int ainv_factor_host(const pcg_grid *grid, const ainv_opts *opts, int32_t *n_wet
   }
 }
 
+}  // extern "C"
+
+// The device side of a handle whose host grid, factor and strips are set:
+// binary64 planes, launch state, pinned mirrors, the staging buffer and its
+// copy stream and events.
+static int handle_device_init(pcg_handle *h, cudaStream_t s) {
+  const size_t cells = (size_t)h->G.nx * h->G.ny;
+  int rc = upload_planes(h, h->p64, s);
+  if (rc) { h->p64.release(); return rc; }
+  if (cudaMalloc(&h->ls, sizeof(LaunchState)) != cudaSuccess) { cudaGetLastError(); h->p64.release(); set_error("device allocation failed"); return PCG_ENOMEM; }
+  if (cudaMallocHost(&h->ls_host, sizeof(LaunchState)) != cudaSuccess ||
+      cudaMallocHost(&h->st_host, sizeof(SolveState)) != cudaSuccess) {
+    cudaGetLastError(); set_error("pinned allocation failed"); return PCG_ENOMEM;
+  }
+  if (cudaMalloc(&h->stage, sizeof(double) * cells) != cudaSuccess) {
+    cudaGetLastError(); set_error("device allocation failed"); return PCG_ENOMEM;
+  }
+  if (cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_unpacked, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_stage, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError(); set_error("stream or event creation failed"); return PCG_ECUDA;
+  }
+  h->bytes = h->p64.bytes + sizeof(LaunchState) + sizeof(double) * cells;
+  CK(cudaStreamSynchronize(s));
+  return PCG_OK;
+}
+
+extern "C" {
+
 int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, pcg_handle **out) {
   if (!out) { set_error("out is NULL"); return PCG_EINVAL; }
   *out = nullptr;
@@ -1096,19 +1156,31 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
       tuned_shape(grid->nx, grid->ny, opts->pattern, opts->band_q, PCG_FP64, 0, &h->tx, &h->ty);
       tuned_shape(grid->nx, grid->ny, opts->pattern, opts->band_q, PCG_MIXED, 0, &h->tx32, &h->ty32);
     }
-    cudaStream_t s = (cudaStream_t)cuda_stream;
-    rc = upload_planes(h.get(), h->p64, s);
-    if (rc) { h->p64.release(); return rc; }
-    if (cudaMalloc(&h->ls, sizeof(LaunchState)) != cudaSuccess) { cudaGetLastError(); h->p64.release(); set_error("device allocation failed"); return PCG_ENOMEM; }
-    if (cudaMallocHost(&h->ls_host, sizeof(LaunchState)) != cudaSuccess ||
-        cudaMallocHost(&h->st_host, sizeof(SolveState)) != cudaSuccess) {
-      cudaGetLastError(); set_error("pinned allocation failed"); return PCG_ENOMEM;
-    }
-    if (cudaMalloc(&h->stage, sizeof(double) * (size_t)grid->nx * grid->ny) != cudaSuccess) {
-      cudaGetLastError(); set_error("device allocation failed"); return PCG_ENOMEM;
-    }
-    h->bytes = h->p64.bytes + sizeof(LaunchState) + sizeof(double) * (size_t)grid->nx * grid->ny;
-    CK(cudaStreamSynchronize(s));
+    if ((rc = handle_device_init(h.get(), (cudaStream_t)cuda_stream))) return rc;
+    *out = h.release();
+    return PCG_OK;
+  } catch (const std::bad_alloc &) {
+    set_error("host allocation failed");
+    return PCG_ENOMEM;
+  }
+}
+
+int pcg_clone(const pcg_handle *src, void *cuda_stream, pcg_handle **out) {
+  if (!out) { set_error("out is NULL"); return PCG_EINVAL; }
+  *out = nullptr;
+  if (!src) { set_error("NULL handle"); return PCG_EINVAL; }
+  try {
+    auto h = std::make_unique<pcg_handle>();
+    handle_init_serial(h.get());
+    h->G = src->G;
+    h->F = src->F;
+    h->pattern = src->pattern;
+    h->band_q = src->band_q;
+    h->tau = src->tau;
+    h->tx = src->tx; h->ty = src->ty;
+    h->tx32 = src->tx32; h->ty32 = src->ty32;
+    int rc = handle_device_init(h.get(), (cudaStream_t)cuda_stream);
+    if (rc) return rc;
     *out = h.release();
     return PCG_OK;
   } catch (const std::bad_alloc &) {
@@ -1326,7 +1398,11 @@ void pcg_free(pcg_handle *h) {
   h->p32.release();
   cudaFreeHost(h->st32_host);
   cudaFree(h->ls);
+  if (h->ev_stage) cudaEventSynchronize(h->ev_stage);
   cudaFree(h->stage);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  for (cudaEvent_t e : {h->ev_in, h->ev_unpacked, h->ev_stage})
+    if (e) cudaEventDestroy(e);
   cudaFreeHost(h->ls_host);
   cudaFreeHost(h->st_host);
   delete h;

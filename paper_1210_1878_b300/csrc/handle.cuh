@@ -182,6 +182,12 @@ struct pcg_handle {
   pcg::LaunchState *ls_host = nullptr;   // pinned
   pcg::SolveState *st_host = nullptr;    // pinned mirror
   double *stage = nullptr;               // device [ny][nx] staging for host buffers
+  // Copies between host buffers and stage. A solve's copies run on the
+  // handle's copy stream, so that they overlap other work on the solve's
+  // stream (another handle's solve); every other call copies on its own stream.
+  // ev_stage marks the last enqueued use of stage, whichever stream it is on.
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_unpacked = nullptr, ev_stage = nullptr;
   std::unique_ptr<pcg::LoopPlan> plan64;
   std::unique_ptr<pcg::LoopPlan> plan32;
   size_t bytes = 0;
@@ -200,12 +206,19 @@ struct Pending {
   std::vector<pcg_handle *> hs;           // members, in call order
   pcg_stats *stats = nullptr;             // caller's [hs.size()] statistics, filled at synchronisation
   cudaStream_t s = nullptr;
+  cudaEvent_t done = nullptr;             // recorded on s after the call's last work there
   bool mixed = false;
   bool graph = false;                     // run by a whole-solve graph (else solved at the call)
   int status = PCG_OK;                    // status of a call solved at the call
   int outer_kernels = 0, inner_kernels = 0;
   LaunchState *ls_host = nullptr;         // pinned copy of the launch state, for the launch count
   std::chrono::steady_clock::time_point t0;
+  Pending() = default;
+  Pending(const Pending &) = delete;
+  Pending &operator=(const Pending &) = delete;
+  ~Pending() {
+    if (done) cudaEventDestroy(done);
+  }
 };
 
 }  // namespace pcg

@@ -421,14 +421,20 @@ namespace {
 
 std::atomic<uint64_t> g_serial{1};
 
-// Wait for h's enqueued solve (if any), fill its call's statistics and
-// release what the call kept alive. Returns the call's status.
+// Wait for h's enqueued solve (if any): the call's work on its stream (not
+// what was queued there after it) and its members' copies back to host
+// buffers. Fill the call's statistics and release what the call kept alive.
+// Returns the call's status.
 int finish_pending(pcg_handle *h) {
   std::shared_ptr<Pending> p = h->pending;
   if (!p) return h->last_status;
   int rc = PCG_OK;
-  if (cudaStreamSynchronize(p->s) != cudaSuccess) {
-    set_error(std::string("solve failed on the device: ") + cudaGetErrorString(cudaGetLastError()));
+  cudaError_t e = p->done ? cudaEventSynchronize(p->done) : cudaStreamSynchronize(p->s);
+  for (pcg_handle *m : p->hs)
+    if (e == cudaSuccess) e = cudaEventSynchronize(m->ev_stage);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    set_error(std::string("solve failed on the device: ") + cudaGetErrorString(e));
     rc = PCG_ECUDA;
   }
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - p->t0).count();
@@ -570,6 +576,8 @@ int pcg_solve_batched(pcg_handle *const *hs, int32_t nbatch, const double *const
     for (auto &m : M)
       if (m.final_status != PCG_OK && first_bad == PCG_OK) first_bad = m.final_status;
     pend->status = first_bad;
+    CK(cudaEventCreateWithFlags(&pend->done, cudaEventDisableTiming));
+    CK(cudaEventRecord(pend->done, s));
     for (pcg_handle *h : members) h->pending = pend;
     return PCG_OK;
   }
@@ -600,6 +608,8 @@ int pcg_solve_batched(pcg_handle *const *hs, int32_t nbatch, const double *const
   pend->graph = true;
   pend->outer_kernels = graph->outer_kernels;
   pend->inner_kernels = graph->inner_kernels;
+  CK(cudaEventCreateWithFlags(&pend->done, cudaEventDisableTiming));
+  CK(cudaEventRecord(pend->done, s));
   for (pcg_handle *h : members) h->pending = pend;
   return PCG_OK;
 }
