@@ -139,7 +139,7 @@ typedef struct pcg_handle pcg_handle;
  * conjugate orthogonalisation (Section 3; the paper builds its factor serially
  * on the CPU, Section 4), and upload A, Z, D^-1 to the device in the packed
  * strip layout. On success *out owns all device memory of this grid.
- * Errors: PCG_EINVAL (nx < 3, nx < 5 with PCG_PAT_TRIL_A2, ny < 1, null
+ * Errors: PCG_EINVAL (nx < 4, nx < 5 with PCG_PAT_TRIL_A2, ny < 1, null
  * pointers, negative or non-finite coefficients, shift <= 0 on a wet cell,
  * PCG_PAT_FULL, band_q out of range), PCG_EBREAKDOWN (non-positive pivot),
  * PCG_ENOMEM, PCG_ECUDA. */

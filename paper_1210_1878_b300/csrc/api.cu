@@ -1128,6 +1128,10 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     handle_init_serial(h.get());
     int rc = factor_host(grid, opts, h->G, h->F);
     if (rc) return rc;
+    if (grid->nx < GHOST) {   // the loop kernels store each column with at most one periodic copy per side
+      set_error("device grids must be at least 4 columns wide");
+      return PCG_EINVAL;
+    }
     h->pattern = opts->pattern;
     h->band_q = opts->band_q;
     h->tau = opts->drop_tol;

@@ -641,28 +641,23 @@ struct K1Geom {
 __host__ __device__ constexpr int fdiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 __host__ __device__ constexpr int pmod(int a, int b) { return ((a % b) + b) % b; }
 
-// A compute thread's column store with its periodic copies. When the grid is
-// at least GHOST wide a column has at most two copies, col + nx (if col <
-// GHOST) and col - nx (if col >= nx - GHOST): predicated stores. Narrower
-// grids take the general loop.
+// A compute thread's column store with its periodic copies. Device grids are
+// at least GHOST columns wide (setup refuses narrower ones), so a column has at
+// most two copies, col + nx (if col < GHOST) and col - nx (if col >= nx -
+// GHOST): two predicated stores, no branch.
 template <typename T>
 struct ColStore {
-  int col, nx, da, db;
-  bool pa, pb, tiny;
+  int col, da, db;
+  bool pa, pb;
   __device__ __forceinline__ void init(int c, int n) {
-    col = c; nx = n;
+    col = c;
     pa = c < GHOST; da = c + n;
     pb = c >= n - GHOST; db = c - n;
-    tiny = n < GHOST;
   }
   __device__ __forceinline__ void put(T *row, T v) const {
     row[col] = v;
-    if (tiny) {
-      store_col(row, col, nx, v, pa, pb);
-    } else {
-      if (pa) row[da] = v;
-      if (pb) row[db] = v;
-    }
+    if (pa) row[da] = v;
+    if (pb) row[db] = v;
   }
 };
 
@@ -791,7 +786,11 @@ struct K1Unit {
         dnm[G::NCG] = v2;
       }
     }
-    if (!compute_sync_and<G::NC>(got)) return false;
+    if constexpr (I == 0) {
+      if (!compute_sync_and<G::NC>(got)) return false;
+    } else {
+      compute_sync<G::NC>();
+    }
     if (waited) ++nseen;
     // row m - 3 is finished: at the last row of its group, release the group
     if constexpr (pmod(K - 2, RB) == 0) {
@@ -1005,6 +1004,9 @@ struct K2Geom {
   static constexpr int NGRP = 1, NC = NGRP * NCG, NT = NC + 32;
   static constexpr size_t SMEM = 128 + 256 + (size_t)NSG * GROUP +
                                  sizeof(T) * ((size_t)NRN * WRC + (size_t)NTT * WTC) + 16 * (NT / 32) + 64;
+  // binary64 strips wider than 64 columns whose ring lets 6 CTAs share an SM
+  // (tril(A) at 124 columns): registers for those 6
+  static constexpr int MINB = (sizeof(T) == 8 && TX > 64 && 6 * (SMEM + 1024) <= 233472) ? 6 : 1;
 };
 
 // One unit of k_precond on the compute side, unrolled by 8 steps like K1Unit.
@@ -1149,7 +1151,11 @@ struct K2Unit {
         rnm[G::NCG] = v2;
       }
     }
-    if (!compute_sync_and<G::NC>(got)) return false;
+    if constexpr (I == 0) {
+      if (!compute_sync_and<G::NC>(got)) return false;
+    } else {
+      compute_sync<G::NC>();
+    }
     if (waited) ++nseen;
     // row m - 2 - LD is finished: at the last row of its group, release the group
     if constexpr (pmod(K - 1 - LD, RB) == 0) {
@@ -1191,7 +1197,7 @@ struct K2Unit {
 };
 
 template <typename T, int TX, class P, int KIND, bool DYN>
-__global__ void __launch_bounds__(K2Geom<T, TX, P>::NT) k_precond(KParams p) {
+__global__ void __launch_bounds__(K2Geom<T, TX, P>::NT, K2Geom<T, TX, P>::MINB) k_precond(KParams p) {
   using G = K2Geom<T, TX, P>;
   constexpr int R = P::R, LD = P::LD, NZ = P::NZ, NW = P::NW;
   extern __shared__ unsigned char smem_raw[];

@@ -63,3 +63,14 @@ def test_host_factor_rejects_invalid_input(mutate, pattern, band_q):
     with pytest.raises(pcg.PCGError) as e:
         pcg.ainv_factor_host(nx, ny, wet, ce, cn, sh, pattern=pattern, band_q=band_q)
     assert e.value.status == pcg.PCG_EINVAL
+
+
+def test_device_setup_refuses_grids_narrower_than_four_columns():
+    """The device layout keeps one periodic copy of a column per side, so a
+    device handle needs nx >= 4; the refusal comes before any device call."""
+    import paper_1210_1878_b300 as pcg
+    nx, ny, wet, ce, cn, sh = _fields(nx=3, ny=5)
+    with pytest.raises(pcg.PCGError) as e:
+        pcg.ainv_setup(nx, ny, wet, ce, cn, sh, pattern=pcg.PCG_PAT_TRIL_A)
+    assert e.value.status == pcg.PCG_EINVAL
+    assert "4 columns" in str(e.value)
