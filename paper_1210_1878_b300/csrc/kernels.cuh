@@ -349,6 +349,15 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parit
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
+// mbar_arrive in the thread where `on` holds, as one predicated instruction
+// (no branch around it)
+__device__ __forceinline__ void mbar_arrive_if(uint64_t *bar, bool on) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.u32 p, %1, 0;\n @p mbarrier.arrive.shared::cta.b64 _, [%0];\n}\n" ::"r"(
+          smem_addr(bar)),
+      "r"((uint32_t)on)
+      : "memory");
+}
 
 // Barrier of the NC compute threads only (named barrier 1), with an AND vote.
 template <int NC>
@@ -795,7 +804,7 @@ struct K1Unit {
     // row m - 3 is finished: at the last row of its group, release the group
     if constexpr (pmod(K - 2, RB) == 0) {
       if (!CHK || rel >= 3) {
-        if (tid == 0) mbar_arrive(&empty[eslot]);
+        mbar_arrive_if(&empty[eslot], tid == 0);
         if (++eslot == (uint32_t)NSG) eslot = 0;
         ++nrel;
       }
@@ -824,7 +833,7 @@ struct K1Unit {
 #undef PCG_K1_STEP
     }
     for (; nrel < ng; ++nrel) {
-      if (tid == 0) mbar_arrive(&empty[eslot]);
+      mbar_arrive_if(&empty[eslot], tid == 0);
       if (++eslot == (uint32_t)NSG) eslot = 0;
     }
     return true;
@@ -1160,7 +1169,7 @@ struct K2Unit {
     // row m - 2 - LD is finished: at the last row of its group, release the group
     if constexpr (pmod(K - 1 - LD, RB) == 0) {
       if (!CHK || rel - 2 - LD >= 0) {
-        if (tid == 0) mbar_arrive(&empty[eslot]);
+        mbar_arrive_if(&empty[eslot], tid == 0);
         if (++eslot == (uint32_t)NSG) eslot = 0;
         ++nrel;
       }
@@ -1189,7 +1198,7 @@ struct K2Unit {
 #undef PCG_K2_STEP
     }
     for (; nrel < ng; ++nrel) {
-      if (tid == 0) mbar_arrive(&empty[eslot]);
+      mbar_arrive_if(&empty[eslot], tid == 0);
       if (++eslot == (uint32_t)NSG) eslot = 0;
     }
     return true;
@@ -1291,7 +1300,8 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT, K2Geom<T, TX, P>::MINB) 
         cx.alpha = (kind == K2_ITER) ? (T)st->alpha : (T)0;
         cx.rout = gdp->r[rsel ^ 1]; cx.s_out = gdp->s; cx.zwrap = gdp->zwrap;
         // the strips holding the first or last columns apply the periodic side table
-        cx.edge = NW > 0 && (i0 < 2 * R + 2 || i0 + TX + 2 * R + 2 > nx);
+        // (a warp vote: the compiler then treats the flag as uniform across the warp)
+        cx.edge = __any_sync(0xffffffffu, NW > 0 && (i0 < 2 * R + 2 || i0 + TX + 2 * R + 2 > nx));
         if (!cx.run()) aborted = true;
         seen = gbase + (uint32_t)cx.nseen;
         acc0 = cx.dot0.total();
