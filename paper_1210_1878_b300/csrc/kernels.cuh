@@ -653,18 +653,19 @@ __host__ __device__ constexpr int pmod(int a, int b) { return ((a % b) + b) % b;
 // A compute thread's column store with its periodic copies. Device grids are
 // at least GHOST columns wide (setup refuses narrower ones), so a column has at
 // most two copies, col + nx (if col < GHOST) and col - nx (if col >= nx -
-// GHOST): two predicated stores, no branch.
+// GHOST). A thread past the strip or the grid (ok = false) stores nothing:
+// three predicated stores, no branch.
 template <typename T>
 struct ColStore {
   int col, da, db;
-  bool pa, pb;
-  __device__ __forceinline__ void init(int c, int n) {
-    col = c;
-    pa = c < GHOST; da = c + n;
-    pb = c >= n - GHOST; db = c - n;
+  bool own, pa, pb;
+  __device__ __forceinline__ void init(int c, int n, bool ok) {
+    col = c; own = ok;
+    pa = ok && c < GHOST; da = c + n;
+    pb = ok && c >= n - GHOST; db = c - n;
   }
   __device__ __forceinline__ void put(T *row, T v) const {
-    row[col] = v;
+    if (own) row[col] = v;
     if (pa) row[da] = v;
     if (pb) row[db] = v;
   }
@@ -732,7 +733,9 @@ struct K1Unit {
     // Loads of a step come before its shared-memory stores: q on row m - 2
     // first (it reads d' rows written in earlier steps), then d' on row m.
     // q = A d' on row r = m - 2 (rel - 3 = r - j0)
-    const bool qrow = (!CHK || (rel >= 3 && rel - 3 < nrows)) && col_ok;
+    // every thread computes (the threads past the strip or the grid read
+    // in-bounds shared memory and store nothing; their dot terms are zero)
+    const bool qrow = !CHK || (rel >= 3 && rel - 3 < nrows);
     if (gb1 && qrow) {
       const unsigned char *br = gb[gback(K, 2)], *bs = gb[gback(K, 3)];
       constexpr int IR = pmod(K - 2, RB), IS = pmod(K - 3, RB);
@@ -753,12 +756,12 @@ struct K1Unit {
         cs.put(d_out + ro, c_ctr);
         if constexpr (G::NGRP == 1) cs.put(x_out + ro, fma(pend, Dr[G::H], Xr[0]));
         cs.put(q_out + ro, av);
-        dot0.add(c_ctr, av);
+        dot0.add(col_ok ? c_ctr : (T)0, col_ok ? av : (T)0);
       } else if (kind == K1_SPMV) {
         cs.put(q_out + ro, av);
       } else {
-        const T bv = Xr[0];
-        const T rv = bv - av;
+        const T bv = col_ok ? Xr[0] : (T)0;
+        const T rv = col_ok ? bv - av : (T)0;
         cs.put(r_out + ro, rv);
         dot0.add(rv, rv);
         dot1.add(bv, bv);
@@ -766,7 +769,7 @@ struct K1Unit {
     }
     if constexpr (G::NGRP == 2 && KIND == K1_ITER) {
       // x += pending d_old on row r (group 0)
-      if (grp == 0 && qrow) {
+      if (grp == 0 && qrow && col_ok) {
         const unsigned char *br = gb[gback(K, 2)];
         constexpr int IR = pmod(K - 2, RB);
         const T *Xr = fld<G::OFF_X>(br, IR, G::WT), *Dr = fld<G::OFF_D>(br, IR, G::WS);
@@ -935,7 +938,7 @@ __global__ void __launch_bounds__(K1Geom<T, TX>::NT) k_stencil(KParams p) {
         cx.mlo = mlo; cx.nr1 = mhi - mlo; cx.nrows = rend - j0; cx.ng = ng;
         cx.pitch = gdp->pitch;
         cx.col_ok = cx.lt < TX && i0 + cx.lt < nx;
-        cx.cs.init(i0 + cx.lt, nx);
+        cx.cs.init(i0 + cx.lt, nx, cx.col_ok);
         cx.beta = (kind == K1_ITER) ? (T)st->beta : (T)0;
         cx.pend = (kind == K1_ITER) ? (T)st->pending : (T)0;
         const int dsel = st->dsel;
@@ -1296,7 +1299,7 @@ __global__ void __launch_bounds__(K2Geom<T, TX, P>::NT, K2Geom<T, TX, P>::MINB) 
         cx.nx = nx; cx.ny = ny; cx.mlo = mlo; cx.j0 = j0; cx.i0 = i0; cx.nr1 = mhi - mlo;
         cx.nrows = rend - j0; cx.ng = ng; cx.pitch = gdp->pitch; cx.col = i0 + cx.lt;
         cx.col_ok = cx.lt < TX && cx.col < nx;
-        cx.cs.init(cx.col, nx);
+        cx.cs.init(cx.col, nx, cx.col_ok);
         cx.alpha = (kind == K2_ITER) ? (T)st->alpha : (T)0;
         cx.rout = gdp->r[rsel ^ 1]; cx.s_out = gdp->s; cx.zwrap = gdp->zwrap;
         // the strips holding the first or last columns apply the periodic side table
