@@ -926,8 +926,9 @@ static int choose_ty(int nx, int ny, int tx, int min_ty) {
 // Measured on 4322 x 3059 (three strip / precision pairs, 7 to 9 heights
 // each), 1442 x 1021, 722 x 511 and 182 x 149 (both precisions, 7 heights),
 // the model's height was the fastest one every time (up to 2.7x faster than
-// a fixed 64 rows for binary32 on small grids).
-static int model_ty(const HostGrid &G, int tx, const KernelSet &ks, int ld) {
+// a fixed 64 rows for binary32 on small grids), except for the 92-column
+// binary64 strips, whose heights are capped (max_unit_rows).
+static int model_ty(const HostGrid &G, int tx, const KernelSet &ks, int ld, int max_ty) {
   constexpr double UNIT_STEPS = 10.0;
   static const int cand[] = {4, 8, 16, 24, 32, 40, 48, 56, 64, 72, 80, 96, 112, 128};
   const int ntx = (G.nx + tx - 1) / tx;
@@ -937,9 +938,10 @@ static int model_ty(const HostGrid &G, int tx, const KernelSet &ks, int ld) {
       if (G.idx[(size_t)j * G.nx + i] >= 0) row_wet[(size_t)(i / tx) * G.ny + j] = 1;
   const int g1 = std::max(ks.ctas1, 1), g2 = std::max(ks.ctas2, 1);
   std::vector<double> c1(g1), c2(g2);
-  int best_ty = 128;
+  int best_ty = max_ty;
   double best = 1e300;
   for (int ty : cand) {
+    if (ty > max_ty) break;                            // (max_unit_rows)
     if ((G.ny + ty - 1) / ty > INT16_MAX) continue;    // strip coordinates are 16-bit
     std::fill(c1.begin(), c1.end(), 0.0);
     std::fill(c2.begin(), c2.end(), 0.0);
@@ -1136,7 +1138,7 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     h->band_q = opts->band_q;
     h->tau = opts->drop_tol;
     if (opts->tile_x != 0 && !valid_width(opts->tile_x, opts->pattern)) {
-      set_error("tile_x must be 64, 128 or a whole-warp width of the pattern (tril(A^2): 60 binary64, 124 "
+      set_error("tile_x must be 64, 128 or a whole-warp width of the pattern (tril(A^2): 60 or 92 binary64, 124 "
                 "binary32; tril(A): 62 or 124 binary64, 124 binary32)");
       return PCG_EINVAL;
     }
@@ -1152,9 +1154,9 @@ int ainv_setup(const pcg_grid *grid, const ainv_opts *opts, void *cuda_stream, p
     if (!opts->tile_y) {                        // heights from the makespan model where the kernels exist
       const int ld = opts->pattern == PCG_PAT_TRIL_A2 ? 2 : (opts->pattern == PCG_PAT_TRIL_A ? 1 : 0);
       KernelSet k64 = pick<double>(h->tx, opts->pattern, opts->band_q);
-      if (k64.ok && prepare_set(k64) == PCG_OK) h->ty = model_ty(h->G, h->tx, k64, ld);
+      if (k64.ok && prepare_set(k64) == PCG_OK) h->ty = model_ty(h->G, h->tx, k64, ld, max_unit_rows(8, h->tx, opts->pattern));
       KernelSet k32 = pick<float>(h->tx32, opts->pattern, opts->band_q);
-      if (k32.ok && prepare_set(k32) == PCG_OK) h->ty32 = model_ty(h->G, h->tx32, k32, ld);
+      if (k32.ok && prepare_set(k32) == PCG_OK) h->ty32 = model_ty(h->G, h->tx32, k32, ld, max_unit_rows(4, h->tx32, opts->pattern));
     }
     if (!opts->tile_x && !opts->tile_y) {       // shapes tuned earlier in this process win (latency objective)
       tuned_shape(grid->nx, grid->ny, opts->pattern, opts->band_q, PCG_FP64, 0, &h->tx, &h->ty);

@@ -51,13 +51,22 @@ inline int exact_width(int elem_size, int pattern) {
   if (elem_size == 8) return pattern == PCG_PAT_TRIL_A2 ? 60 : 62;
   return 124;
 }
-// A wider binary64 strip for tril(A): 124 columns, whose r' pass is 128
-// columns (4 whole warps) and whose t pass is 126; its ring is small enough
-// for 5 CTAs per SM, and on wide grids it beats two 62-column strips (fewer
-// halo columns per point). tril(A^2)'s ring at this width leaves 3 CTAs per
-// SM, which is slower than 60.
+// Wider binary64 strips, used on wide grids: for tril(A) 124 columns, whose r'
+// pass is 128 columns (4 whole warps) and whose t pass is 126; its ring is
+// small enough for 5 CTAs per SM, and it beats two 62-column strips (fewer
+// halo columns per point). For tril(A^2) 92 columns (t pass 96 = 3 whole
+// warps, 4 CTAs per SM): 3 % fewer FP64 instructions per point than 60-column
+// strips, and faster with units of at most 64 rows; at 124 columns its ring
+// leaves 3 CTAs per SM, which is slower.
 inline int wide_width(int elem_size, int pattern) {
-  return (elem_size == 8 && pattern == PCG_PAT_TRIL_A) ? 124 : 0;
+  if (elem_size != 8) return 0;
+  return pattern == PCG_PAT_TRIL_A ? 124 : pattern == PCG_PAT_TRIL_A2 ? 92 : 0;
+}
+// Tallest unit the makespan model may choose for a strip width: the 92-column
+// binary64 tril(A^2) strips measured fastest with 48-64 rows at 4322 x 3059
+// (0.577-0.581 ms per iteration, against 0.594 at the model's 96 and 0.606 at 128).
+inline int max_unit_rows(int elem_size, int tx, int pattern) {
+  return (elem_size == 8 && pattern == PCG_PAT_TRIL_A2 && tx == wide_width(8, pattern)) ? 64 : 128;
 }
 inline bool valid_width(int tx, int pattern) {
   return tx == 64 || tx == 128 || tx == exact_width(8, pattern) || tx == exact_width(4, pattern) ||

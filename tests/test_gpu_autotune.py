@@ -34,8 +34,8 @@ def test_autotune_applies_and_remembers(prec):
     g = gridgen.make_grid(seed=gridgen.seed_for(5), **CFG)
     h = pcg.ainv_setup_grid(g, pattern=pcg.PCG_PAT_TRIL_A2, drop_tol=0.05)
     tx, ty = pcg.pcg_autotune(h, prec)
-    # candidates: 64, 128 and the whole-warp width of tril(A^2) (60 binary64, 124 binary32)
-    assert tx in (64, 128, 60 if prec == 0 else 124) and ty in (8, 16, 32, 64)
+    # candidates: 64, 128 and the whole-warp widths of tril(A^2) (60 and 92 binary64, 124 binary32)
+    assert tx in ((64, 128, 60, 92) if prec == 0 else (64, 128, 124)) and ty in (8, 16, 32, 64)
     assert pcg.pcg_tiles(h, prec) == (tx, ty)
     _check_solve(pcg, h, g, prec)
     # a later handle of the same grid shape starts with the tuned strips

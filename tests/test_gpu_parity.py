@@ -69,15 +69,17 @@ PRECONDS = [(0, 0.0, 0), (1, 0.0, 0), (1, 0.05, 0), (4, 0.0, 0), (3, 0.0, 1), (3
 
 @pytest.mark.parametrize("spec", GRIDS, ids=[g[0] for g in GRIDS])
 @pytest.mark.parametrize("pattern,tau,q", PRECONDS)
-@pytest.mark.parametrize("tile_x", [0, 64, 124])
+@pytest.mark.parametrize("tile_x", [0, 64, 124, 92])
 def test_precond_matches_oracle(spec, pattern, tau, q, tile_x):
     """tile_x 0: the default strips (60/62 columns for tril(A^2)/tril(A), whose
-    t phase fills whole warps); 64: strips with a halo pass; 124: the wide
-    binary64 strip of tril(A)."""
+    t phase fills whole warps); 64: strips with a halo pass; 124 and 92: the wide
+    binary64 strips of tril(A) and tril(A^2)."""
     pcg = _pcg()
     g = _grid(spec)
     if tile_x == 124 and pattern != pcg.PCG_PAT_TRIL_A:
         pytest.skip("124-column binary64 strips exist for tril(A) only")
+    if tile_x == 92 and pattern != pcg.PCG_PAT_TRIL_A2:
+        pytest.skip("92-column binary64 strips exist for tril(A^2) only")
     if pattern == 3 and q >= g.nx:
         pytest.skip("band wider than the row")
     P = oracle.OracleProblem.from_grid(g)
@@ -105,6 +107,7 @@ SOLVES = [
     ("ragged-trilA", dict(nx=203, ny=77, land=0.3), 7, 0, 0.0, 0, 0),
     ("ragged-trilA2", dict(nx=203, ny=77, land=0.3), 7, 1, 0.05, 0, 0),
     ("ragged-trilA-wide", dict(nx=203, ny=77, land=0.3), 7, 0, 0.0, 0, 124),   # 124-column strips
+    ("ragged-trilA2-wide", dict(nx=203, ny=77, land=0.3), 7, 1, 0.05, 0, 92),   # 92-column strips
     ("orca1-trilA2", dict(gridgen.ORCA1), 3, 1, 0.05, 0, 0),
     ("orca025-trilA2", dict(gridgen.ORCA025), 2, 1, 0.05, 0, 0),
 ]
