@@ -100,8 +100,9 @@ typedef struct {
   int32_t tile_x;      /* device strip width in points: 64, 128, or a width whose preconditioner pass
                           fills whole warps (tril(A^2): 60 or 92 binary64 / 124 binary32; tril(A): 62 or
                           124 binary64 / 124 binary32), applied to the precisions that have it (the other
-                          keeps its default); 0 = chosen per precision (binary64: 92 for tril(A^2) and 124
-                          for tril(A) on grids of 2048 columns or more, else 60 / 62) */
+                          keeps its default); 0 = chosen per precision (binary64: 92 for tril(A^2) on grids
+                          of 700 columns or more, 124 for tril(A) on grids of 2048 columns or more, else
+                          60 / 62) */
   int32_t tile_y;      /* device strip height in rows, 4..256; 0 = chosen per precision at setup: the height
                           (4..128) minimising a model of the two loop launches' slowest CTA / SM over the
                           grid's wet strips and the resident CTAs (a shape tuned earlier wins) */

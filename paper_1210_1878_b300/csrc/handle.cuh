@@ -51,7 +51,7 @@ inline int exact_width(int elem_size, int pattern) {
   if (elem_size == 8) return pattern == PCG_PAT_TRIL_A2 ? 60 : 62;
   return 124;
 }
-// Wider binary64 strips, used on wide grids: for tril(A) 124 columns, whose r'
+// Wider binary64 strips, used on wide grids (see choose_tx): for tril(A) 124 columns, whose r'
 // pass is 128 columns (4 whole warps) and whose t pass is 126; its ring is
 // small enough for 5 CTAs per SM, and it beats two 62-column strips (fewer
 // halo columns per point). For tril(A^2) 92 columns (t pass 96 = 3 whole
